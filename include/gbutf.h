@@ -1,0 +1,152 @@
+/*
+ * gbutf: validating UTF-8 <-> UTF-16LE transcoding on NVIDIA GB300 (sm_103a).
+ *
+ * A C ABI over hand-written CUDA kernels. The operations are those of
+ * Clausecker & Lemire, "Transcoding Unicode Characters with AVX-512
+ * Instructions" (arXiv 2212.05098): transcode a buffer of UTF-8 into UTF-16LE
+ * (Sec. 6) or UTF-16LE into UTF-8 (Sec. 7), validating the input throughout
+ * (Sec. 6.4, Sec. 7.4); on an encoding error, transcode the valid prefix and
+ * report the number of input units before the first error (Sec. 6.4,
+ * Sec. 7.5). The length-only calls run the same validation and count the
+ * output without writing it.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Units. UTF-8 is counted in bytes, UTF-16LE in 16-bit words (little endian,
+ *   no byte-order mark generated, checked or stripped; Sec. 2.1).
+ * - Validity. UTF-8 follows Table 1 and rules 1-6 of Sec. 6.4 (shortest form,
+ *   no surrogates, nothing above U+10FFFF, C0/C1/F5-FF never valid). UTF-16LE
+ *   requires every high surrogate to be followed by a low surrogate and every
+ *   low surrogate to be preceded by a high one. Noncharacters (U+FFFE ...) and
+ *   U+0000 are valid.
+ * - Result (gbu_result):
+ *     GBU_OK                in_offset = n, out_len = output units written.
+ *     encoding error kind   in_offset = index of the first invalid input unit
+ *                           (the lead byte of a malformed or truncated
+ *                           sequence, a stray continuation byte, or the
+ *                           unpaired surrogate); out_len = output units of
+ *                           the valid prefix [0, in_offset). An encoding error
+ *                           takes precedence over a too-small output.
+ *     GBU_OUTPUT_TOO_SMALL  the input is valid but needs out_len > cap units;
+ *                           in_offset = n.
+ *     GBU_INVALID_ARG, GBU_DEVICE_ERROR, GBU_DEVICE_TIMEOUT: in_offset = 0,
+ *                           out_len = 0, output contents unspecified.
+ *   Output: units [0, min(out_len, cap)) are written exactly; units from
+ *   out_len to cap are unspecified; nothing at or beyond cap is written.
+ *   Error kinds are this library's convention (the paper defines only the
+ *   error position): byte class first, then structure, then value.
+ * - Memory. d_in / d_out are device pointers owned by the caller (any
+ *   allocation the current CUDA context can read / write; e.g. torch
+ *   tensors). UTF-8 buffers may have any alignment; UTF-16 buffers must be
+ *   2-byte aligned (else GBU_INVALID_ARG). Input and output must not overlap.
+ *   The kernels read whole aligned 16-byte blocks that overlap the input
+ *   range (never a block disjoint from it).
+ * - Worst-case capacity: UTF-8 -> UTF-16 needs at most n_bytes units;
+ *   UTF-16 -> UTF-8 at most 3 * n_units bytes.
+ * - Size limit: n < 2^39 input units per call (else GBU_INVALID_ARG).
+ * - Streams. `stream` is a cudaStream_t (0 = legacy default stream). The
+ *   synchronous calls enqueue on it and wait for that stream only.
+ * - Contexts. A gbu_ctx owns device scratch memory (scan state, error word,
+ *   result slot). Calls on one context must not overlap on the GPU: use one
+ *   context per stream (or per concurrently running call). Contexts are not
+ *   thread-safe.
+ * - No exceptions cross this interface; CUDA errors become GBU_DEVICE_ERROR.
+ */
+#ifndef GBUTF_H
+#define GBUTF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gbu_status {
+    GBU_OK = 0,
+    GBU_HEADER_BITS = 1,          /* byte F5-FF (UTF-8 rule 1)                      */
+    GBU_TOO_SHORT = 2,            /* lead byte without all its continuation bytes    */
+    GBU_TOO_LONG = 3,             /* continuation byte with no lead (rule 3)         */
+    GBU_OVERLONG = 4,             /* C0/C1, or a 3/4-byte form of a smaller value    */
+    GBU_TOO_LARGE = 5,            /* value above U+10FFFF (rule 5)                   */
+    GBU_SURROGATE = 6,            /* UTF-8 encoding of U+D800-U+DFFF (rule 6)        */
+    GBU_LONE_HIGH_SURROGATE = 7,  /* UTF-16 high surrogate not followed by a low     */
+    GBU_LONE_LOW_SURROGATE = 8,   /* UTF-16 low surrogate not preceded by a high     */
+    GBU_OUTPUT_TOO_SMALL = 16,
+    GBU_INVALID_ARG = 17,
+    GBU_DEVICE_ERROR = 18,
+    GBU_DEVICE_TIMEOUT = 19       /* a bounded wait inside a kernel gave up          */
+} gbu_status;
+
+typedef struct gbu_result {
+    int32_t status;      /* gbu_status                                          */
+    uint32_t reserved;   /* zero                                                */
+    uint64_t in_offset;  /* see "Result" above                                  */
+    uint64_t out_len;    /* output units (UTF-16: words; UTF-8: bytes)          */
+} gbu_result;
+
+typedef struct gbu_ctx gbu_ctx;
+
+/* Create a context on CUDA device `device` (that device becomes current for
+ * the calling thread). Returns NULL on failure. Free with gbu_destroy. */
+gbu_ctx *gbu_create(int device);
+void gbu_destroy(gbu_ctx *ctx);
+
+/* Pre-size the context's scratch memory for inputs of up to `max_input_bytes`
+ * bytes, so that later calls allocate nothing. Scratch grows on demand
+ * otherwise (a growth synchronises the device). Returns a gbu_status. */
+int32_t gbu_reserve(gbu_ctx *ctx, uint64_t max_input_bytes);
+
+/* UTF-8 -> UTF-16LE (Sec. 6). d_in: n_bytes bytes; d_out: cap_units words. */
+gbu_result gbu_utf8_to_utf16le(gbu_ctx *ctx, const uint8_t *d_in, uint64_t n_bytes,
+                               uint16_t *d_out, uint64_t cap_units, void *stream);
+
+/* UTF-16LE -> UTF-8 (Sec. 7). d_in: n_units words; d_out: cap_bytes bytes. */
+gbu_result gbu_utf16le_to_utf8(gbu_ctx *ctx, const uint16_t *d_in, uint64_t n_units,
+                               uint8_t *d_out, uint64_t cap_bytes, void *stream);
+
+/* Validating length-only calls: out_len = UTF-16 words (resp. UTF-8 bytes) of
+ * the whole input, or of its valid prefix on an encoding error. */
+gbu_result gbu_utf16_length_from_utf8(gbu_ctx *ctx, const uint8_t *d_in, uint64_t n_bytes,
+                                      void *stream);
+gbu_result gbu_utf8_length_from_utf16le(gbu_ctx *ctx, const uint16_t *d_in, uint64_t n_units,
+                                        void *stream);
+
+/* Asynchronous forms: enqueue the work on `stream` and return at once. The
+ * gbu_result is stored to `result` (device memory, or pinned host memory
+ * mapped into the device's address space) when the stream reaches the end of
+ * the work. Return value: GBU_OK if enqueued, else GBU_INVALID_ARG /
+ * GBU_DEVICE_ERROR (nothing enqueued, `result` untouched). */
+int32_t gbu_utf8_to_utf16le_async(gbu_ctx *ctx, const uint8_t *d_in, uint64_t n_bytes,
+                                  uint16_t *d_out, uint64_t cap_units,
+                                  gbu_result *result, void *stream);
+int32_t gbu_utf16le_to_utf8_async(gbu_ctx *ctx, const uint16_t *d_in, uint64_t n_units,
+                                  uint8_t *d_out, uint64_t cap_bytes,
+                                  gbu_result *result, void *stream);
+int32_t gbu_utf16_length_from_utf8_async(gbu_ctx *ctx, const uint8_t *d_in, uint64_t n_bytes,
+                                         gbu_result *result, void *stream);
+int32_t gbu_utf8_length_from_utf16le_async(gbu_ctx *ctx, const uint16_t *d_in,
+                                           uint64_t n_units, gbu_result *result,
+                                           void *stream);
+
+/* Host-buffer forms: h_in / h_out are host memory (pinned memory gives the
+ * fastest copies). The call copies the input to device scratch owned by the
+ * context, transcodes it there, and copies min(out_len, cap) output units
+ * back into h_out, all on `stream`, and returns when done. */
+gbu_result gbu_utf8_to_utf16le_host(gbu_ctx *ctx, const uint8_t *h_in, uint64_t n_bytes,
+                                    uint16_t *h_out, uint64_t cap_units, void *stream);
+gbu_result gbu_utf16le_to_utf8_host(gbu_ctx *ctx, const uint16_t *h_in, uint64_t n_units,
+                                    uint8_t *h_out, uint64_t cap_bytes, void *stream);
+
+/* Name of a gbu_status value ("GBU_OK", ...); "GBU_UNKNOWN" otherwise. */
+const char *gbu_status_name(int32_t status);
+
+/* Number of kernels this library has launched in the calling process
+ * (diagnostics; counts every launch of every entry point). */
+uint64_t gbu_kernel_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBUTF_H */

@@ -1,0 +1,226 @@
+"""Python binding of libgbutf (validating UTF-8 <-> UTF-16LE transcoding on GB300).
+
+Argument marshalling only: every function here forwards to the C ABI of
+``include/gbutf.h`` with the same name, passing raw device pointers, sizes
+and the CUDA stream handle. All transcoding work runs in the library's CUDA
+kernels. There is no fallback: if the library cannot be built or loaded, the
+import of the function raises.
+
+Convenience wrappers (``Context.utf8_to_utf16le`` ...) take torch CUDA tensors
+and allocate worst-case outputs; torch provides device memory and streams only.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+from . import build as _build
+
+GBU_OK = 0
+GBU_HEADER_BITS = 1
+GBU_TOO_SHORT = 2
+GBU_TOO_LONG = 3
+GBU_OVERLONG = 4
+GBU_TOO_LARGE = 5
+GBU_SURROGATE = 6
+GBU_LONE_HIGH_SURROGATE = 7
+GBU_LONE_LOW_SURROGATE = 8
+GBU_OUTPUT_TOO_SMALL = 16
+GBU_INVALID_ARG = 17
+GBU_DEVICE_ERROR = 18
+GBU_DEVICE_TIMEOUT = 19
+
+
+class gbu_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("reserved", ctypes.c_uint32),
+                ("in_offset", ctypes.c_uint64), ("out_len", ctypes.c_uint64)]
+
+
+@dataclass(frozen=True)
+class Result:
+    status: int
+    in_offset: int
+    out_len: int
+
+    @property
+    def ok(self) -> bool:
+        return self.status == GBU_OK
+
+    @property
+    def name(self) -> str:
+        return status_name(self.status)
+
+
+# name -> (restype, argtypes)
+_VP, _U64, _I32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int32
+_RP = ctypes.POINTER(gbu_result)
+SIGNATURES = {
+    "gbu_create": (_VP, [ctypes.c_int]),
+    "gbu_destroy": (None, [_VP]),
+    "gbu_reserve": (_I32, [_VP, _U64]),
+    "gbu_utf8_to_utf16le": (gbu_result, [_VP, _VP, _U64, _VP, _U64, _VP]),
+    "gbu_utf16le_to_utf8": (gbu_result, [_VP, _VP, _U64, _VP, _U64, _VP]),
+    "gbu_utf16_length_from_utf8": (gbu_result, [_VP, _VP, _U64, _VP]),
+    "gbu_utf8_length_from_utf16le": (gbu_result, [_VP, _VP, _U64, _VP]),
+    "gbu_utf8_to_utf16le_async": (_I32, [_VP, _VP, _U64, _VP, _U64, _VP, _VP]),
+    "gbu_utf16le_to_utf8_async": (_I32, [_VP, _VP, _U64, _VP, _U64, _VP, _VP]),
+    "gbu_utf16_length_from_utf8_async": (_I32, [_VP, _VP, _U64, _VP, _VP]),
+    "gbu_utf8_length_from_utf16le_async": (_I32, [_VP, _VP, _U64, _VP, _VP]),
+    "gbu_utf8_to_utf16le_host": (gbu_result, [_VP, _VP, _U64, _VP, _U64, _VP]),
+    "gbu_utf16le_to_utf8_host": (gbu_result, [_VP, _VP, _U64, _VP, _U64, _VP]),
+    "gbu_status_name": (ctypes.c_char_p, [_I32]),
+    "gbu_kernel_launch_count": (_U64, []),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libgbutf.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.build() if build_if_missing else _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libgbutf.so not found at {path}; run build()")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _res(r: gbu_result) -> Result:
+    return Result(int(r.status), int(r.in_offset), int(r.out_len))
+
+
+# ---- raw C-ABI mirrors (same names, integer pointers) -----------------------
+
+def gbu_create(device: int = 0) -> int:
+    h = load().gbu_create(device)
+    if not h:
+        raise RuntimeError(f"gbu_create({device}) failed")
+    return h
+
+
+def gbu_destroy(ctx: int) -> None:
+    load().gbu_destroy(ctx)
+
+
+def gbu_reserve(ctx: int, max_input_bytes: int) -> int:
+    return load().gbu_reserve(ctx, max_input_bytes)
+
+
+def gbu_utf8_to_utf16le(ctx, d_in, n_bytes, d_out, cap_units, stream=0) -> Result:
+    return _res(load().gbu_utf8_to_utf16le(ctx, d_in, n_bytes, d_out, cap_units, stream))
+
+
+def gbu_utf16le_to_utf8(ctx, d_in, n_units, d_out, cap_bytes, stream=0) -> Result:
+    return _res(load().gbu_utf16le_to_utf8(ctx, d_in, n_units, d_out, cap_bytes, stream))
+
+
+def gbu_utf16_length_from_utf8(ctx, d_in, n_bytes, stream=0) -> Result:
+    return _res(load().gbu_utf16_length_from_utf8(ctx, d_in, n_bytes, stream))
+
+
+def gbu_utf8_length_from_utf16le(ctx, d_in, n_units, stream=0) -> Result:
+    return _res(load().gbu_utf8_length_from_utf16le(ctx, d_in, n_units, stream))
+
+
+def gbu_utf8_to_utf16le_async(ctx, d_in, n_bytes, d_out, cap_units, d_result, stream=0) -> int:
+    return load().gbu_utf8_to_utf16le_async(ctx, d_in, n_bytes, d_out, cap_units, d_result, stream)
+
+
+def gbu_utf16le_to_utf8_async(ctx, d_in, n_units, d_out, cap_bytes, d_result, stream=0) -> int:
+    return load().gbu_utf16le_to_utf8_async(ctx, d_in, n_units, d_out, cap_bytes, d_result, stream)
+
+
+def gbu_utf16_length_from_utf8_async(ctx, d_in, n_bytes, d_result, stream=0) -> int:
+    return load().gbu_utf16_length_from_utf8_async(ctx, d_in, n_bytes, d_result, stream)
+
+
+def gbu_utf8_length_from_utf16le_async(ctx, d_in, n_units, d_result, stream=0) -> int:
+    return load().gbu_utf8_length_from_utf16le_async(ctx, d_in, n_units, d_result, stream)
+
+
+def gbu_utf8_to_utf16le_host(ctx, h_in, n_bytes, h_out, cap_units, stream=0) -> Result:
+    return _res(load().gbu_utf8_to_utf16le_host(ctx, h_in, n_bytes, h_out, cap_units, stream))
+
+
+def gbu_utf16le_to_utf8_host(ctx, h_in, n_units, h_out, cap_bytes, stream=0) -> Result:
+    return _res(load().gbu_utf16le_to_utf8_host(ctx, h_in, n_units, h_out, cap_bytes, stream))
+
+
+def gbu_kernel_launch_count() -> int:
+    return int(load().gbu_kernel_launch_count())
+
+
+def status_name(status: int) -> str:
+    return load().gbu_status_name(status).decode()
+
+
+# ---- torch convenience layer (device memory + streams only) -------------------
+
+def _stream_handle(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+class Context:
+    """Owns one gbu_ctx (scratch for one in-flight call) on one device."""
+
+    def __init__(self, device: int = 0):
+        self.device = device
+        self.handle = gbu_create(device)
+
+    def close(self):
+        if self.handle:
+            gbu_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):  # pragma: no cover - interpreter shutdown order
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reserve(self, max_input_bytes: int) -> None:
+        st = gbu_reserve(self.handle, max_input_bytes)
+        if st != GBU_OK:
+            raise RuntimeError(f"gbu_reserve failed: {status_name(st)}")
+
+    def utf8_to_utf16le(self, src, out=None, stream=None):
+        """src: uint8 CUDA tensor. Returns (Result, int16 tensor holding the words)."""
+        import torch
+        n = src.numel()
+        if out is None:
+            out = torch.empty(max(n, 1), dtype=torch.int16, device=src.device)
+        r = gbu_utf8_to_utf16le(self.handle, src.data_ptr(), n, out.data_ptr(), out.numel(),
+                                _stream_handle(stream))
+        return r, out
+
+    def utf16le_to_utf8(self, src, out=None, stream=None):
+        """src: int16/uint16-sized CUDA tensor of words. Returns (Result, uint8 tensor)."""
+        import torch
+        n = src.numel()
+        if out is None:
+            out = torch.empty(max(3 * n, 1), dtype=torch.uint8, device=src.device)
+        r = gbu_utf16le_to_utf8(self.handle, src.data_ptr(), n, out.data_ptr(), out.numel(),
+                                _stream_handle(stream))
+        return r, out
+
+    def utf16_length_from_utf8(self, src, stream=None) -> Result:
+        return gbu_utf16_length_from_utf8(self.handle, src.data_ptr(), src.numel(),
+                                          _stream_handle(stream))
+
+    def utf8_length_from_utf16le(self, src, stream=None) -> Result:
+        return gbu_utf8_length_from_utf16le(self.handle, src.data_ptr(), src.numel(),
+                                            _stream_handle(stream))

@@ -1,0 +1,335 @@
+// C ABI of the library (declared in include/gbutf.h): contexts, scratch
+// management and the synchronous / asynchronous / host-buffer entry points.
+// Every step of the transcoding runs in the kernels of utf8_to_utf16.cu and
+// utf16_to_utf8.cu; this file only validates arguments, sizes scratch and
+// enqueues work.
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "../../include/gbutf.h"
+#include "kernels.h"
+
+using namespace gbu;
+
+static_assert(sizeof(gbu_result) == sizeof(ResultSlot), "result layout");
+static_assert((int)GBU_DEVICE_TIMEOUT == (int)kDeviceTimeout &&
+                  (int)GBU_LONE_LOW_SURROGATE == (int)kLoneLow,
+              "status numbering");
+
+namespace {
+
+std::atomic<uint64_t> g_launches{0};
+
+constexpr uint64_t kMaxUnits = 1ull << 39;
+constexpr size_t kHeaderBytes = 256;   // claim, done, flags, err, spare
+
+gbu_result make(int32_t st, uint64_t off = 0, uint64_t len = 0)
+{
+    gbu_result r;
+    r.status = st;
+    r.reserved = 0;
+    r.in_offset = off;
+    r.out_len = len;
+    return r;
+}
+
+}  // namespace
+
+struct gbu_ctx {
+    int device = 0;
+    uint8_t *scratch = nullptr;       // header + status[] + err_prefix[]
+    uint64_t max_chunks = 0;
+    uint32_t epoch = 0;
+    bool dirty = true;                // header needs re-initialisation
+    gbu_result *h_result = nullptr;   // pinned, mapped
+    gbu_result *d_result = nullptr;   // device alias of h_result
+    uint8_t *io = nullptr;            // device staging for the host-buffer forms
+    size_t io_bytes = 0;
+};
+
+namespace {
+
+bool ok(cudaError_t e) { return e == cudaSuccess; }
+
+Scratch scratch_of(gbu_ctx *c)
+{
+    Scratch s;
+    s.claim = reinterpret_cast<unsigned int *>(c->scratch);
+    s.done = s.claim + 1;
+    s.flags = s.claim + 2;
+    s.err = reinterpret_cast<unsigned long long *>(c->scratch + 16);
+    s.status = reinterpret_cast<unsigned long long *>(c->scratch + kHeaderBytes);
+    s.err_prefix = s.status + c->max_chunks;
+    return s;
+}
+
+// Make sure scratch covers `chunks` chunks; (re)initialise the header.
+int32_t ensure_scratch(gbu_ctx *c, uint64_t chunks, cudaStream_t stream)
+{
+    if (chunks > c->max_chunks) {
+        uint64_t want = c->max_chunks ? c->max_chunks : 256;
+        while (want < chunks) want *= 2;
+        if (c->scratch) {
+            if (!ok(cudaStreamSynchronize(stream)) || !ok(cudaDeviceSynchronize()))
+                return GBU_DEVICE_ERROR;
+            cudaFree(c->scratch);
+            c->scratch = nullptr;
+        }
+        if (!ok(cudaMalloc(&c->scratch, kHeaderBytes + 16 * want))) {
+            c->max_chunks = 0;
+            return GBU_DEVICE_ERROR;
+        }
+        c->max_chunks = want;
+        if (!ok(cudaMemset(c->scratch, 0, kHeaderBytes + 16 * want))) return GBU_DEVICE_ERROR;
+        c->epoch = 0;
+        c->dirty = true;
+    }
+    if (c->dirty) {
+        // claim = done = flags = 0, err = ~0
+        static const uint64_t hdr[4] = {0, 0, ~0ull, 0};
+        if (!ok(cudaMemcpyAsync(c->scratch, hdr, sizeof hdr, cudaMemcpyHostToDevice, stream)))
+            return GBU_DEVICE_ERROR;
+        c->dirty = false;
+    }
+    if (++c->epoch > kEpochMask) {   // epoch wrap: clear the status words once
+        if (!ok(cudaMemsetAsync(c->scratch + kHeaderBytes, 0, 8 * c->max_chunks, stream)))
+            return GBU_DEVICE_ERROR;
+        c->epoch = 1;
+    }
+    return GBU_OK;
+}
+
+enum class Op { U8toU16, U16toU8 };
+
+// Enqueue one call; result goes to `dst` (device-visible).
+int32_t enqueue(gbu_ctx *c, Op op, const void *in, uint64_t n, void *out, uint64_t cap,
+                bool write, ResultSlot *dst, cudaStream_t stream)
+{
+    if (!c || !dst || (n && !in) || (write && cap && !out)) return GBU_INVALID_ARG;
+    if (n >= kMaxUnits) return GBU_INVALID_ARG;
+    if (op == Op::U16toU8 && (reinterpret_cast<uintptr_t>(in) & 1u)) return GBU_INVALID_ARG;
+    if (op == Op::U8toU16 && write && (reinterpret_cast<uintptr_t>(out) & 1u)) return GBU_INVALID_ARG;
+    if (!ok(cudaSetDevice(c->device))) return GBU_DEVICE_ERROR;
+    if (n == 0) {
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+        return ok(launch_write_result(dst, GBU_OK, 0, 0, stream)) ? GBU_OK : GBU_DEVICE_ERROR;
+    }
+    Launch L{};
+    const void *base;
+    if (op == Op::U8toU16)
+        base = plan_utf8(static_cast<const uint8_t *>(in), n, L);
+    else
+        base = plan_utf16(static_cast<const uint16_t *>(in), n, L);
+    int32_t st = ensure_scratch(c, L.num_chunks, stream);
+    if (st != GBU_OK) {
+        c->dirty = true;
+        return st;
+    }
+    L.s = scratch_of(c);
+    L.result = dst;
+    L.cap = write ? cap : 0;
+    L.epoch = c->epoch;
+    cudaError_t e;
+    if (op == Op::U8toU16)
+        e = launch_utf8_to_utf16(static_cast<const uint8_t *>(base), static_cast<uint16_t *>(out),
+                                 write, L, stream);
+    else
+        e = launch_utf16_to_utf8(static_cast<const uint16_t *>(base), static_cast<uint8_t *>(out),
+                                 write, L, stream);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (!ok(e)) {
+        c->dirty = true;
+        return GBU_DEVICE_ERROR;
+    }
+    return GBU_OK;
+}
+
+gbu_result run_sync(gbu_ctx *c, Op op, const void *in, uint64_t n, void *out, uint64_t cap,
+                    bool write, void *stream)
+{
+    if (!c) return make(GBU_INVALID_ARG);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (n == 0) return make(GBU_OK, 0, 0);
+    int32_t st = enqueue(c, op, in, n, out, cap, write,
+                         reinterpret_cast<ResultSlot *>(c->d_result), s);
+    if (st != GBU_OK) return make(st);
+    if (!ok(cudaStreamSynchronize(s))) {
+        c->dirty = true;
+        return make(GBU_DEVICE_ERROR);
+    }
+    gbu_result r;
+    std::memcpy(&r, const_cast<const gbu_result *>(c->h_result), sizeof r);
+    if (r.status == GBU_DEVICE_TIMEOUT || r.status == GBU_DEVICE_ERROR) c->dirty = true;
+    return r;
+}
+
+}  // namespace
+
+extern "C" {
+
+gbu_ctx *gbu_create(int device)
+{
+    gbu_ctx *c = new (std::nothrow) gbu_ctx();
+    if (!c) return nullptr;
+    c->device = device;
+    void *h = nullptr;
+    if (!ok(cudaSetDevice(device)) ||
+        !ok(cudaHostAlloc(&h, sizeof(gbu_result), cudaHostAllocMapped))) {
+        delete c;
+        return nullptr;
+    }
+    c->h_result = static_cast<gbu_result *>(h);
+    std::memset(c->h_result, 0, sizeof(gbu_result));
+    void *d = nullptr;
+    if (!ok(cudaHostGetDevicePointer(&d, h, 0))) {
+        cudaFreeHost(h);
+        delete c;
+        return nullptr;
+    }
+    c->d_result = static_cast<gbu_result *>(d);
+    return c;
+}
+
+void gbu_destroy(gbu_ctx *c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    if (c->scratch) cudaFree(c->scratch);
+    if (c->io) cudaFree(c->io);
+    if (c->h_result) cudaFreeHost(c->h_result);
+    delete c;
+}
+
+int32_t gbu_reserve(gbu_ctx *c, uint64_t max_input_bytes)
+{
+    if (!c) return GBU_INVALID_ARG;
+    if (!ok(cudaSetDevice(c->device))) return GBU_DEVICE_ERROR;
+    const uint64_t chunks = (max_input_bytes + 16 + kChunk8 - 1) / kChunk8 + 1;
+    int32_t st = ensure_scratch(c, chunks, nullptr);
+    if (st == GBU_OK && !ok(cudaDeviceSynchronize())) st = GBU_DEVICE_ERROR;
+    return st;
+}
+
+gbu_result gbu_utf8_to_utf16le(gbu_ctx *c, const uint8_t *d_in, uint64_t n, uint16_t *d_out,
+                               uint64_t cap, void *stream)
+{
+    return run_sync(c, Op::U8toU16, d_in, n, d_out, cap, true, stream);
+}
+
+gbu_result gbu_utf16le_to_utf8(gbu_ctx *c, const uint16_t *d_in, uint64_t n, uint8_t *d_out,
+                               uint64_t cap, void *stream)
+{
+    return run_sync(c, Op::U16toU8, d_in, n, d_out, cap, true, stream);
+}
+
+gbu_result gbu_utf16_length_from_utf8(gbu_ctx *c, const uint8_t *d_in, uint64_t n, void *stream)
+{
+    return run_sync(c, Op::U8toU16, d_in, n, nullptr, 0, false, stream);
+}
+
+gbu_result gbu_utf8_length_from_utf16le(gbu_ctx *c, const uint16_t *d_in, uint64_t n,
+                                        void *stream)
+{
+    return run_sync(c, Op::U16toU8, d_in, n, nullptr, 0, false, stream);
+}
+
+int32_t gbu_utf8_to_utf16le_async(gbu_ctx *c, const uint8_t *d_in, uint64_t n, uint16_t *d_out,
+                                  uint64_t cap, gbu_result *result, void *stream)
+{
+    return enqueue(c, Op::U8toU16, d_in, n, d_out, cap, true,
+                   reinterpret_cast<ResultSlot *>(result), static_cast<cudaStream_t>(stream));
+}
+
+int32_t gbu_utf16le_to_utf8_async(gbu_ctx *c, const uint16_t *d_in, uint64_t n, uint8_t *d_out,
+                                  uint64_t cap, gbu_result *result, void *stream)
+{
+    return enqueue(c, Op::U16toU8, d_in, n, d_out, cap, true,
+                   reinterpret_cast<ResultSlot *>(result), static_cast<cudaStream_t>(stream));
+}
+
+int32_t gbu_utf16_length_from_utf8_async(gbu_ctx *c, const uint8_t *d_in, uint64_t n,
+                                         gbu_result *result, void *stream)
+{
+    return enqueue(c, Op::U8toU16, d_in, n, nullptr, 0, false,
+                   reinterpret_cast<ResultSlot *>(result), static_cast<cudaStream_t>(stream));
+}
+
+int32_t gbu_utf8_length_from_utf16le_async(gbu_ctx *c, const uint16_t *d_in, uint64_t n,
+                                           gbu_result *result, void *stream)
+{
+    return enqueue(c, Op::U16toU8, d_in, n, nullptr, 0, false,
+                   reinterpret_cast<ResultSlot *>(result), static_cast<cudaStream_t>(stream));
+}
+
+static gbu_result run_host(gbu_ctx *c, Op op, const void *h_in, uint64_t n, void *h_out,
+                           uint64_t cap, void *stream)
+{
+    if (!c || (n && !h_in) || (cap && !h_out)) return make(GBU_INVALID_ARG);
+    if (n == 0) return make(GBU_OK, 0, 0);
+    if (n >= kMaxUnits) return make(GBU_INVALID_ARG);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!ok(cudaSetDevice(c->device))) return make(GBU_DEVICE_ERROR);
+    const size_t in_bytes = op == Op::U8toU16 ? n : 2 * n;
+    const size_t ub = op == Op::U8toU16 ? 2 : 1;
+    const size_t in_al = (in_bytes + 255) & ~size_t(255);
+    const size_t need = in_al + cap * ub + 16;
+    if (need > c->io_bytes) {
+        if (!ok(cudaStreamSynchronize(s))) return make(GBU_DEVICE_ERROR);
+        if (c->io) cudaFree(c->io);
+        c->io = nullptr;
+        c->io_bytes = 0;
+        if (!ok(cudaMalloc(&c->io, need))) return make(GBU_DEVICE_ERROR);
+        c->io_bytes = need;
+    }
+    uint8_t *d_in = c->io, *d_out = c->io + in_al;
+    if (!ok(cudaMemcpyAsync(d_in, h_in, in_bytes, cudaMemcpyHostToDevice, s)))
+        return make(GBU_DEVICE_ERROR);
+    gbu_result r = run_sync(c, op, d_in, n, d_out, cap, true, stream);
+    if (r.status >= GBU_INVALID_ARG) return r;
+    const uint64_t keep = r.out_len < cap ? r.out_len : cap;
+    if (keep) {
+        if (!ok(cudaMemcpyAsync(h_out, d_out, keep * ub, cudaMemcpyDeviceToHost, s)) ||
+            !ok(cudaStreamSynchronize(s)))
+            return make(GBU_DEVICE_ERROR);
+    }
+    return r;
+}
+
+gbu_result gbu_utf8_to_utf16le_host(gbu_ctx *c, const uint8_t *h_in, uint64_t n, uint16_t *h_out,
+                                    uint64_t cap, void *stream)
+{
+    return run_host(c, Op::U8toU16, h_in, n, h_out, cap, stream);
+}
+
+gbu_result gbu_utf16le_to_utf8_host(gbu_ctx *c, const uint16_t *h_in, uint64_t n, uint8_t *h_out,
+                                    uint64_t cap, void *stream)
+{
+    return run_host(c, Op::U16toU8, h_in, n, h_out, cap, stream);
+}
+
+const char *gbu_status_name(int32_t s)
+{
+    switch (s) {
+    case GBU_OK: return "GBU_OK";
+    case GBU_HEADER_BITS: return "GBU_HEADER_BITS";
+    case GBU_TOO_SHORT: return "GBU_TOO_SHORT";
+    case GBU_TOO_LONG: return "GBU_TOO_LONG";
+    case GBU_OVERLONG: return "GBU_OVERLONG";
+    case GBU_TOO_LARGE: return "GBU_TOO_LARGE";
+    case GBU_SURROGATE: return "GBU_SURROGATE";
+    case GBU_LONE_HIGH_SURROGATE: return "GBU_LONE_HIGH_SURROGATE";
+    case GBU_LONE_LOW_SURROGATE: return "GBU_LONE_LOW_SURROGATE";
+    case GBU_OUTPUT_TOO_SMALL: return "GBU_OUTPUT_TOO_SMALL";
+    case GBU_INVALID_ARG: return "GBU_INVALID_ARG";
+    case GBU_DEVICE_ERROR: return "GBU_DEVICE_ERROR";
+    case GBU_DEVICE_TIMEOUT: return "GBU_DEVICE_TIMEOUT";
+    default: return "GBU_UNKNOWN";
+    }
+}
+
+uint64_t gbu_kernel_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+}  // extern "C"

@@ -78,39 +78,56 @@ UTF8 = "utf8"
 UTF16 = "utf16le"
 
 
-def _rng(seed: int) -> np.random.Generator:
-    return np.random.Generator(np.random.Philox(key=int(seed)))
+def _rng(seed: int, block: int = 0) -> np.random.Generator:
+    return np.random.Generator(np.random.Philox(key=[int(seed), int(block)]))
 
 
 def _unit_bytes(encoding: str) -> int:
     return 1 if encoding == UTF8 else 2
 
 
+# Characters per independently keyed block: block b of seed s is drawn from
+# Philox with key (s, b), so any block can be produced on its own and the text
+# does not depend on how blocks are spread over worker processes.
+BLOCK = 1 << 22
+
+
+def _draw_block(profile: str, seed: int, block: int, n: int = BLOCK):
+    """Code points and category indices of one block of `n` characters."""
+    cats = PROFILES[profile]
+    # interleaved (category, offset) pairs: the first n characters of a block
+    # do not depend on how many are drawn
+    u = _rng(seed, block).integers(0, 1 << 32, size=(n, 2), dtype=np.uint32)
+    u1, u2 = u[:, 0], u[:, 1].astype(np.uint64)
+    cat = np.zeros(n, dtype=np.uint8)
+    acc = 0.0
+    for c in cats[:-1]:
+        acc += c.prob
+        cat += (u1 >= np.uint32(min(int(acc * 2.0**32), (1 << 32) - 1))).astype(np.uint8)
+    sizes = np.array([c.size for c in cats], dtype=np.uint64)
+    off = (u2 * sizes[cat]) >> np.uint64(32)          # uniform in [0, size)
+    cps = np.empty(n, dtype=np.uint32)
+    for k, c in enumerate(cats):
+        m = cat == k
+        o = off[m].astype(np.int64)
+        if len(c.ranges) == 1:
+            cps[m] = (c.ranges[0][0] + o).astype(np.uint32)
+        else:
+            widths = np.array([hi - lo + 1 for lo, hi in c.ranges], dtype=np.int64)
+            base = np.concatenate([[0], np.cumsum(widths)[:-1]])
+            los = np.array([lo for lo, _ in c.ranges], dtype=np.int64)
+            idx = np.searchsorted(base, o, side="right") - 1
+            cps[m] = (los[idx] + (o - base[idx])).astype(np.uint32)
+    return cps, cat
+
+
 def draw_chars(profile: str, n_chars: int, seed: int):
     """Return (code points uint32[n_chars], category index uint8[n_chars])."""
-    cats = PROFILES[profile]
-    rng = _rng(seed)
-    cum = np.cumsum([c.prob for c in cats])
-    cum[-1] = 1.0
-    u = rng.random(n_chars, dtype=np.float64)
-    cat = np.searchsorted(cum, u, side="right").astype(np.uint8)
-    np.minimum(cat, len(cats) - 1, out=cat)
-    cps = np.empty(n_chars, dtype=np.uint32)
-    for k, c in enumerate(cats):
-        idx = np.nonzero(cat == k)[0]
-        if idx.size == 0:
-            continue
-        r = rng.integers(0, c.size, size=idx.size, dtype=np.int64)
-        # map a uniform index into the union of the category's ranges
-        vals = np.empty(idx.size, dtype=np.int64)
-        base = 0
-        for lo, hi in c.ranges:
-            w = hi - lo + 1
-            m = (r >= base) & (r < base + w)
-            vals[m] = lo + (r[m] - base)
-            base += w
-        cps[idx] = vals.astype(np.uint32)
-    return cps, cat
+    parts = [_draw_block(profile, seed, b, min(BLOCK, n_chars - b * BLOCK))
+             for b in range((n_chars + BLOCK - 1) // BLOCK)]
+    if not parts:
+        return np.zeros(0, np.uint32), np.zeros(0, np.uint8)
+    return np.concatenate([p[0] for p in parts]), np.concatenate([p[1] for p in parts])
 
 
 def encode(cps: np.ndarray, encoding: str) -> np.ndarray:
@@ -120,15 +137,22 @@ def encode(cps: np.ndarray, encoding: str) -> np.ndarray:
     return np.frombuffer(b, dtype=np.uint8)
 
 
+def _encoded_block(profile: str, seed: int, block: int, encoding: str, keep_cps: bool,
+                   n: int = BLOCK, keep_cat: bool = True):
+    cps, cat = _draw_block(profile, seed, block, n)
+    data = encode(cps, encoding).tobytes()
+    return data, (cat if keep_cat else None), (cps if keep_cps else None)
+
+
 @dataclass
 class Text:
     profile: str
     encoding: str
     seed: int
     data: np.ndarray            # uint8 bytes in `encoding`
-    cps: np.ndarray             # code points, including the U+0020 padding
-    in_len: np.ndarray          # uint8 input units per character (this encoding)
-    out_len: np.ndarray         # uint8 output units per character (other encoding)
+    in_len: np.ndarray | None   # uint8 input units per character (this encoding)
+    out_len: np.ndarray | None  # uint8 output units per character (other encoding)
+    cps: np.ndarray | None = None   # code points incl. padding (when requested)
 
     @property
     def n_units(self) -> int:
@@ -146,12 +170,16 @@ class Text:
         return s
 
 
-def generate(profile: str, target_bytes: int, encoding: str, seed: int | None = None) -> Text:
+def generate(profile: str, target_bytes: int, encoding: str, seed: int | None = None,
+             executor=None, keep_cps: bool = True, keep_lens: bool = True) -> Text:
     """Seeded text of exactly `target_bytes` bytes in `encoding`.
 
     Characters are appended until the next one would pass the target, then the
     text is padded with U+0020 to the exact size (the target must be even for
-    UTF-16LE).
+    UTF-16LE). `executor` (a concurrent.futures executor, e.g. a process pool
+    started with "spawn") draws blocks in parallel; the text is the same either
+    way. With keep_lens=False (large benchmark inputs) the per-character
+    length arrays are not kept.
     """
     if seed is None:
         seed = PROFILE_SEED[profile]
@@ -163,26 +191,87 @@ def generate(profile: str, target_bytes: int, encoding: str, seed: int | None = 
     in_tab = np.array([c.utf8_len if encoding == UTF8 else c.utf16_len for c in cats], np.uint8)
     out_tab = np.array([c.utf16_len if encoding == UTF8 else c.utf8_len for c in cats], np.uint8)
     mean = sum(c.prob * int(in_tab[k]) for k, c in enumerate(cats))
-    n_draw = int(target_units / mean * 1.02) + 64
-    cps, cat = draw_chars(profile, n_draw, seed)
-    in_len = in_tab[cat]
-    cum = np.cumsum(in_len, dtype=np.int64)
-    k = int(np.searchsorted(cum, target_units, side="right"))
-    if k == n_draw and cum[-1] < target_units:
-        raise RuntimeError("generator under-drew; increase the margin")
-    used = int(cum[k - 1]) if k else 0
+    n_blocks = int(target_units / (mean * BLOCK) * 1.01) + 1
+
+    blocks = []
+    have = 0
+    b = 0
+    if target_units < 0.9 * mean * BLOCK:
+        # small text: the needed prefix of block 0 (the same characters)
+        n0 = min(BLOCK, int(target_units / mean * 1.05) + 256)
+        data, cat, cps = _encoded_block(profile, seed, 0, encoding, keep_cps, n0)
+        if len(data) // ub >= target_units:
+            blocks.append((data, cat, cps))
+            have = target_units
+    while have < target_units:
+        todo = list(range(b, b + max(1, n_blocks - b)))
+        if executor is not None and len(todo) > 1:
+            futs = [executor.submit(_encoded_block, profile, seed, k, encoding, keep_cps,
+                                    BLOCK, keep_lens) for k in todo]
+            got = [f.result() for f in futs]
+        else:
+            got = [_encoded_block(profile, seed, k, encoding, keep_cps, BLOCK, keep_lens)
+                   for k in todo]
+        for data, cat, cps in got:
+            if have >= target_units:
+                break
+            blocks.append((data, cat, cps))
+            have += len(data) // ub
+        b = todo[-1] + 1
+        n_blocks = b + 1
+
+    # cut inside the last block at the last character that still fits
+    datas, cats_l, cps_l = [], [], []
+    used = 0
+    for data, cat, cps in blocks:
+        units = len(data) // ub
+        if used + units <= target_units:
+            datas.append(np.frombuffer(data, np.uint8))
+            cats_l.append(cat)
+            if cps is not None:
+                cps_l.append(cps)
+            used += units
+            continue
+        if cat is None:   # redraw the last block's categories here (same key)
+            cat = _draw_block(profile, seed, len(datas), BLOCK)[1]
+        lens = in_tab[cat]
+        cum = np.cumsum(lens, dtype=np.int64)
+        k = int(np.searchsorted(cum, target_units - used, side="right"))
+        take = int(cum[k - 1]) if k else 0
+        datas.append(np.frombuffer(data, np.uint8)[: take * ub])
+        cats_l.append(cat[:k])
+        if cps is not None:
+            cps_l.append(cps[:k])
+        used += take
+        break
     pad = target_units - used
-    cps = np.concatenate([cps[:k], np.full(pad, 0x20, np.uint32)])
-    space = np.ones(pad, np.uint8)
-    in_len = np.concatenate([in_len[:k], space])
-    out_len = np.concatenate([out_tab[cat[:k]], space])
-    data = encode(cps, encoding)
+    space = np.full(pad, 0x20, np.uint32)
+    datas.append(encode(space, encoding))
+    data = np.concatenate(datas)
     assert data.size == target_bytes
-    return Text(profile, encoding, seed, np.array(data), cps, in_len, out_len)
+    in_len = out_len = None
+    if keep_lens:
+        cat_all = np.concatenate(cats_l) if cats_l else np.zeros(0, np.uint8)
+        ones = np.ones(pad, np.uint8)
+        in_len = np.concatenate([in_tab[cat_all], ones])
+        out_len = np.concatenate([out_tab[cat_all], ones])
+    cps_all = np.concatenate(cps_l + [space]) if keep_cps else None
+    return Text(profile, encoding, seed, data, in_len, out_len, cps_all)
+
+
+def process_pool(workers: int | None = None):
+    """A process pool started with "spawn" (safe after CUDA initialisation)."""
+    import multiprocessing
+    import os
+    from concurrent.futures import ProcessPoolExecutor
+    if workers is None:
+        workers = max(1, min(16, (os.cpu_count() or 2) - 1))
+    return ProcessPoolExecutor(max_workers=workers,
+                               mp_context=multiprocessing.get_context("spawn"))
 
 
 def random_bytes(n: int, seed: int) -> np.ndarray:
-    return _rng(seed).integers(0, 256, size=n, dtype=np.uint8)
+    return _rng(seed, 1 << 40).integers(0, 256, size=n, dtype=np.uint8)
 
 
 def mutate(data: np.ndarray, n_flips: int, seed: int) -> np.ndarray:
@@ -190,7 +279,7 @@ def mutate(data: np.ndarray, n_flips: int, seed: int) -> np.ndarray:
     out = np.array(data, copy=True)
     if out.size == 0 or n_flips <= 0:
         return out
-    rng = _rng(seed)
+    rng = _rng(seed, 1 << 41)
     pos = rng.integers(0, out.size, size=n_flips)
     out[pos] = rng.integers(0, 256, size=n_flips, dtype=np.uint8)
     return out

@@ -138,6 +138,24 @@ gbu_result gbu_utf8_to_utf16le_host(gbu_ctx *ctx, const uint8_t *h_in, uint64_t 
 gbu_result gbu_utf16le_to_utf8_host(gbu_ctx *ctx, const uint16_t *h_in, uint64_t n_units,
                                     uint8_t *h_out, uint64_t cap_bytes, void *stream);
 
+/* No-allocation form of gbu_utf8_to_utf16le. The paper has no counterpart to
+ * this call: it is for callers that may not allocate device memory (another
+ * component owns the device's memory, or an allocation's implicit device
+ * synchronisation is not acceptable on their path), whereas gbu_create /
+ * gbu_reserve allocate scratch. It takes no context: the kernel's scratch is
+ * one fixed-size device array inside this library, held by every GPU that
+ * loads the library until the process exits, so inputs are limited to
+ * GBU_NOALLOC_MAX_BYTES bytes (larger inputs: GBU_INVALID_ARG, nothing run).
+ * The first call on a device looks up the array's device address and clears
+ * it; make that first call before any stream capture. All calls share the
+ * array: calls that overlap on the GPU (other streams, other host threads on
+ * the same device) race and must not be issued. Same arguments, result and
+ * output rules as gbu_utf8_to_utf16le; calls no cudaMalloc / cudaFree; waits
+ * for `stream`. Its launches are not counted by gbu_kernel_launch_count. */
+#define GBU_NOALLOC_MAX_BYTES (64ull << 20)
+gbu_result gbu_utf8_to_utf16le_noalloc(const uint8_t *d_in, uint64_t n_bytes,
+                                       uint16_t *d_out, uint64_t cap_units, void *stream);
+
 /* Name of a gbu_status value ("GBU_OK", ...); "GBU_UNKNOWN" otherwise. */
 const char *gbu_status_name(int32_t status);
 

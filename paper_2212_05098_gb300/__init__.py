@@ -69,6 +69,7 @@ SIGNATURES = {
     "gbu_utf8_length_from_utf16le_async": (_I32, [_VP, _VP, _U64, _VP, _VP]),
     "gbu_utf8_to_utf16le_host": (gbu_result, [_VP, _VP, _U64, _VP, _U64, _VP]),
     "gbu_utf16le_to_utf8_host": (gbu_result, [_VP, _VP, _U64, _VP, _U64, _VP]),
+    "gbu_utf8_to_utf16le_noalloc": (gbu_result, [_VP, _U64, _VP, _U64, _VP]),
     "gbu_status_name": (ctypes.c_char_p, [_I32]),
     "gbu_kernel_launch_count": (_U64, []),
 }
@@ -155,6 +156,13 @@ def gbu_utf8_to_utf16le_host(ctx, h_in, n_bytes, h_out, cap_units, stream=0) -> 
 
 def gbu_utf16le_to_utf8_host(ctx, h_in, n_units, h_out, cap_bytes, stream=0) -> Result:
     return _res(load().gbu_utf16le_to_utf8_host(ctx, h_in, n_units, h_out, cap_bytes, stream))
+
+
+def gbu_utf8_to_utf16le_noalloc(d_in, n_bytes, d_out, cap_units, stream=0) -> Result:
+    return _res(load().gbu_utf8_to_utf16le_noalloc(d_in, n_bytes, d_out, cap_units, stream))
+
+
+GBU_NOALLOC_MAX_BYTES = 64 << 20
 
 
 def gbu_kernel_launch_count() -> int:

@@ -1,0 +1,121 @@
+// UTF-8 -> UTF-16LE for callers that must not allocate device memory.
+//
+// Some callers cannot call cudaMalloc: code that runs where another component
+// owns all of the device's memory (a framework's caching allocator, a memory
+// budget fixed at start-up), code that must never trigger the implicit device
+// synchronisation an allocation can cause (latency-critical request paths), or
+// plug-ins that are not allowed to own device memory at all. gbu_create /
+// gbu_reserve allocate scratch, so those callers get this entry point instead.
+//
+// It runs the same kernel as gbu_utf8_to_utf16le, but the kernel's scratch
+// (chunk counters, first-error word, look-back status words, per-chunk error
+// prefixes and the result slot) lives in one file-scope device array of fixed
+// size, which every GPU that loads this library holds until the process exits.
+// That fixes the largest input: GBU_NOALLOC_MAX_BYTES.
+//
+// In host code the array's name only stands in for the symbol; it is not a
+// device address. Its device address is looked up with cudaGetSymbolAddress
+// once per device, with that device current, on the first call made on that
+// device; that first call also clears the array. Make that first call before
+// any stream capture.
+#include <cstring>
+#include <mutex>
+
+#include "../../include/gbutf.h"
+#include "kernels.h"
+
+using namespace gbu;
+
+namespace {
+
+constexpr uint64_t kNoAllocChunks = (GBU_NOALLOC_MAX_BYTES + 15 + kChunk8 - 1) / kChunk8;
+constexpr size_t kHeader = 256;   // claim, done, flags | err | result slot | spare
+constexpr size_t kScratchBytes = kHeader + 16 * kNoAllocChunks;
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+struct DeviceState {
+    unsigned char *base = nullptr;   // device address of g_noalloc_scratch
+    uint32_t epoch = 0;
+};
+
+std::mutex g_mu;
+DeviceState g_dev[kMaxDevices];
+
+gbu_result fail(int32_t st)
+{
+    gbu_result r;
+    r.status = st;
+    r.reserved = 0;
+    r.in_offset = 0;
+    r.out_len = 0;
+    return r;
+}
+
+}  // namespace
+
+extern "C" gbu_result gbu_utf8_to_utf16le_noalloc(const uint8_t *d_in, uint64_t n_bytes,
+                                                  uint16_t *d_out, uint64_t cap_units,
+                                                  void *stream)
+{
+    if ((n_bytes && !d_in) || (cap_units && !d_out)) return fail(GBU_INVALID_ARG);
+    if (n_bytes > GBU_NOALLOC_MAX_BYTES) return fail(GBU_INVALID_ARG);
+    if (reinterpret_cast<uintptr_t>(d_out) & 1u) return fail(GBU_INVALID_ARG);
+    if (n_bytes == 0) {
+        gbu_result r = fail(GBU_OK);
+        return r;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+        return fail(GBU_DEVICE_ERROR);
+
+    Launch L{};
+    const uint8_t *base_in = plan_utf8(d_in, n_bytes, L);
+    if (L.num_chunks > kNoAllocChunks) return fail(GBU_INVALID_ARG);
+
+    unsigned char *base;
+    {
+        std::lock_guard<std::mutex> lock(g_mu);
+        DeviceState &d = g_dev[dev];
+        if (!d.base) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p)
+                return fail(GBU_DEVICE_ERROR);
+            // status words must start "not ready" for every epoch
+            if (cudaMemsetAsync(p, 0, kScratchBytes, s) != cudaSuccess)
+                return fail(GBU_DEVICE_ERROR);
+            d.base = static_cast<unsigned char *>(p);
+            d.epoch = 0;
+        }
+        if (++d.epoch > kEpochMask) {   // epoch wrap: clear the status words once
+            if (cudaMemsetAsync(d.base + kHeader, 0, 8 * kNoAllocChunks, s) != cudaSuccess)
+                return fail(GBU_DEVICE_ERROR);
+            d.epoch = 1;
+        }
+        base = d.base;
+        L.epoch = d.epoch;
+    }
+    // The array keeps whatever the previous call left: counters and flags must
+    // start at zero and the first-error word at all ones.
+    if (cudaMemsetAsync(base, 0, 16, s) != cudaSuccess ||
+        cudaMemsetAsync(base + 16, 0xFF, 8, s) != cudaSuccess)
+        return fail(GBU_DEVICE_ERROR);
+
+    L.s.claim = reinterpret_cast<unsigned int *>(base);
+    L.s.done = L.s.claim + 1;
+    L.s.flags = L.s.claim + 2;
+    L.s.err = reinterpret_cast<unsigned long long *>(base + 16);
+    L.s.status = reinterpret_cast<unsigned long long *>(base + kHeader);
+    L.s.err_prefix = L.s.status + kNoAllocChunks;
+    L.result = reinterpret_cast<ResultSlot *>(base + 64);
+    L.cap = cap_units;
+    if (launch_utf8_to_utf16(base_in, d_out, true, L, s) != cudaSuccess)
+        return fail(GBU_DEVICE_ERROR);
+    gbu_result r;
+    if (cudaMemcpyAsync(&r, base + 64, sizeof r, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return fail(GBU_DEVICE_ERROR);
+    return r;
+}

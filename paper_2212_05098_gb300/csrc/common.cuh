@@ -203,18 +203,17 @@ __device__ __forceinline__ uint32_t mask_word_bytes(uint32_t w, int64_t vpos, in
     return w & keep;
 }
 
-// End of a launch: every CTA counts itself done; the last one assembles the
-// gbu_result from the scan totals and the first-error word, stores it, and
-// resets the counters for the next launch on this scratch.
+// End of a launch, called by thread 0 of every CTA after its last status /
+// error-word writes: count the CTA done; the last one assembles the
+// gbu_result from the scan total and the first-error word, stores it, and
+// resets the counters for the next launch on this scratch. Only the scan and
+// error words need ordering before the done count (the output itself is not
+// read by the finisher), so one thread fences, not the whole CTA.
 template <bool kWrite>
 __device__ __forceinline__ void finish_launch(const Launch &L, uint32_t chunk_elems)
 {
-    __shared__ unsigned int s_last;
     __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = (atomicAdd(L.s.done, 1u) == gridDim.x - 1) ? 1u : 0u;
-    __syncthreads();
-    if (!s_last || threadIdx.x != 0) return;
+    if (atomicAdd(L.s.done, 1u) != gridDim.x - 1) return;
     __threadfence();
     const uint64_t total = ld_relaxed(&L.s.status[L.num_chunks - 1]) & kValueMask;
     const uint64_t err = ld_relaxed(L.s.err);
@@ -245,6 +244,46 @@ __device__ __forceinline__ void finish_launch(const Launch &L, uint32_t chunk_el
     *L.s.flags = 0;
     st_relaxed(L.s.err, ~0ull);
     __threadfence_system();
+}
+
+// First-error key inside a CTA: position (39 bits) | kind (8 bits) | output
+// units of the chunk before the error (15 bits). Positions are unique, so the
+// minimum key is the first error and carries its prefix length along.
+__device__ __forceinline__ uint64_t err_key(uint64_t pos, uint32_t kind, uint32_t units)
+{
+    return (pos << 23) | ((uint64_t)kind << 15) | (units & 0x7FFFu);
+}
+
+// Thread 0, after the look-back: publish the chunk's first error (if any)
+// into the per-chunk prefix slot and the grid-wide first-error word.
+__device__ __forceinline__ void publish_error(const Launch &L, uint32_t chunk, uint64_t key,
+                                              uint64_t excl)
+{
+    if (key == ~0ull) return;
+    const uint64_t pos = key >> 23;
+    const uint32_t kind = (uint32_t)(key >> 15) & 0xFFu;
+    L.s.err_prefix[chunk] = excl + (key & 0x7FFFu);
+    atomicMin(L.s.err, (pos << 8) | kind);
+}
+
+// PTX prmt.b32 (generic mode): byte k of the result is byte sel[4k+2:4k] of
+// the 8-byte value {b, a}; when sel bit 4k+3 is set, that byte's sign bit is
+// replicated over the 8 bits instead. (The __byte_perm intrinsic ignores the
+// sign bit of the selector, hence the inline PTX.)
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel)
+{
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+    return d;
+}
+
+// Byte-wise helpers on little-endian 32-bit words holding 4 input bytes.
+// zero_bytes(v): bit 7 of every byte of v that is zero. Exact when no byte of
+// v can be 0x01 directly above a zero byte (callers pass values whose bytes
+// are even or multiples of 0x10); otherwise a superset, used only for flags.
+__device__ __forceinline__ uint32_t zero_bytes(uint32_t v)
+{
+    return (v - 0x01010101u) & ~v & 0x80808080u;
 }
 
 }  // namespace gbu

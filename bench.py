@@ -46,8 +46,8 @@ METRIC = "input GB/s, validated UTF-8<->UTF-16LE transcoding (4 profiles x 2 dir
 WORKLOAD = ("single 1 GiB buffer per text profile (latin, cyrillic, cjk, emoji), both directions "
             "(UTF-8->UTF-16LE, UTF-16LE->UTF-8), validated")
 DIRS = ("utf8_to_utf16le", "utf16le_to_utf8")
-KERNEL_OF = {"utf8_to_utf16le": "utf8_to_utf16_kernel", "utf16le_to_utf8": "utf16_to_utf8_kernel"}
-KERNEL_SRC = {"utf8_to_utf16_kernel": "utf8_to_utf16.cu", "utf16_to_utf8_kernel": "utf16_to_utf8.cu"}
+KERNEL = "transcode_kernel"      # the one persistent kernel (both directions)
+KERNEL_SRC = {"transcode_kernel": "transcode.cu"}
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -328,35 +328,34 @@ def main():
     bytes_step = sum(c["data"].size for c in cases)
     value = world * bytes_step * K / (ms_total / 1e3) / 1e9
 
-    # per-kernel launch times and the dominant kernel's roofline
-    per_kernel = {}
+    # the kernel's roofline over all its launches, with a per-direction split
+    peak, peak_src = measured_peak()
+    per_dir = {}
     for i, c in enumerate(cases):
-        kname = KERNEL_OF[c["dir"]]
-        d = per_kernel.setdefault(kname, {"ms": 0.0, "bytes": 0, "in_bytes": 0, "launches": 0})
+        d = per_dir.setdefault(c["dir"], {"ms": 0.0, "bytes": 0, "in_bytes": 0, "launches": 0})
         for k in range(K):
             d["ms"] += ev[k][i][0].elapsed_time(ev[k][i][1])
             d["bytes"] += c["alg_bytes"]
             d["in_bytes"] += c["data"].size
             d["launches"] += 1
-    dom = max(per_kernel, key=lambda k: per_kernel[k]["ms"])
-    peak, peak_src = measured_peak()
-    kernels = {}
-    for kname, d in per_kernel.items():
-        ach = d["bytes"] / (d["ms"] / 1e3) / 1e9
-        ratio = traffic_record(kname)
-        kernels[kname] = {
-            "achieved_gbs": ach, "frac": ach / peak,
-            "avg_launch_ms": d["ms"] / d["launches"],
-            "alg_bytes_per_launch": d["bytes"] / d["launches"],
-            "traffic_per_launch": (ratio * d["in_bytes"] / d["launches"]) if ratio else None,
-            "share_of_time": d["ms"] / sum(x["ms"] for x in per_kernel.values()),
-        }
-    kd = kernels[dom]
-    roofline = {"kernel": dom, "bound": "hbm", "achieved": kd["achieved_gbs"], "peak": peak,
-                "unit": "GB/s", "frac": kd["frac"], "traffic": kd["traffic_per_launch"],
+    tot_ms = sum(x["ms"] for x in per_dir.values())
+    tot_bytes = sum(x["bytes"] for x in per_dir.values())
+    tot_in = sum(x["in_bytes"] for x in per_dir.values())
+    n_launch = sum(x["launches"] for x in per_dir.values())
+    ratio = traffic_record(KERNEL)
+    achieved = tot_bytes / (tot_ms / 1e3) / 1e9
+    directions = {dname: {"achieved_gbs": d["bytes"] / (d["ms"] / 1e3) / 1e9,
+                          "frac": d["bytes"] / (d["ms"] / 1e3) / 1e9 / peak,
+                          "avg_launch_ms": d["ms"] / d["launches"],
+                          "alg_bytes_per_launch": d["bytes"] / d["launches"],
+                          "share_of_time": d["ms"] / tot_ms}
+                  for dname, d in per_dir.items()}
+    roofline = {"kernel": KERNEL, "bound": "hbm", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak,
+                "traffic": (ratio * tot_in / n_launch) if ratio else None,
                 "peak_source": peak_src,
-                "algorithmic_bytes_per_launch": kd["alg_bytes_per_launch"],
-                "avg_launch_ms": kd["avg_launch_ms"]}
+                "algorithmic_bytes_per_launch": tot_bytes / n_launch,
+                "avg_launch_ms": tot_ms / n_launch}
     per_case = {f"{c['profile']}/{c['dir']}":
                 c["data"].size / (statistics.median(ev[k][i][0].elapsed_time(ev[k][i][1])
                                                     for k in range(K)) / 1e3) / 1e9
@@ -415,7 +414,7 @@ def main():
                        "parallelism": f"independent buffers per rank x {world}",
                        "l2": "inputs 1 GiB each, larger than the 129 MB L2; no flush"},
             "roofline": roofline,
-            "kernels": kernels,
+            "directions": directions,
             "per_buffer_input_gbs": per_case,
             "cpu_baseline": cpu,
             "e2e": e2e,

@@ -23,7 +23,6 @@ namespace {
 std::atomic<uint64_t> g_launches{0};
 
 constexpr uint64_t kMaxUnits = 1ull << 39;
-constexpr size_t kHeaderBytes = 256;   // claim, done, flags, err, spare
 
 gbu_result make(int32_t st, uint64_t off = 0, uint64_t len = 0)
 {
@@ -41,7 +40,6 @@ struct gbu_ctx {
     int device = 0;
     uint8_t *scratch = nullptr;       // header + status[] + err_prefix[]
     uint64_t max_chunks = 0;
-    uint32_t epoch = 0;
     bool dirty = true;                // header needs re-initialisation
     gbu_result *h_result = nullptr;   // pinned, mapped
     gbu_result *d_result = nullptr;   // device alias of h_result
@@ -53,16 +51,19 @@ namespace {
 
 bool ok(cudaError_t e) { return e == cudaSuccess; }
 
-Scratch scratch_of(gbu_ctx *c)
+// Point a one-item job at the context's scratch.
+void attach_scratch(gbu_ctx *c, Job &J)
 {
-    Scratch s;
-    s.claim = reinterpret_cast<unsigned int *>(c->scratch);
-    s.done = s.claim + 1;
-    s.flags = s.claim + 2;
-    s.err = reinterpret_cast<unsigned long long *>(c->scratch + 16);
-    s.status = reinterpret_cast<unsigned long long *>(c->scratch + kHeaderBytes);
-    s.err_prefix = s.status + c->max_chunks;
-    return s;
+    uint8_t *h = c->scratch;
+    J.claim = reinterpret_cast<unsigned int *>(h + kHdrClaim);
+    J.exit_count = reinterpret_cast<unsigned int *>(h + kHdrExit);
+    J.flags = reinterpret_cast<unsigned int *>(h + kHdrFlags);
+    J.item_done = reinterpret_cast<unsigned int *>(h + kHdrDone);
+    J.item_err = reinterpret_cast<unsigned long long *>(h + kHdrErr);
+    J.epoch = reinterpret_cast<unsigned int *>(h + kHdrEpoch);
+    J.status = reinterpret_cast<unsigned long long *>(h + kHeaderBytes);
+    J.status_capacity = (uint32_t)c->max_chunks;
+    J.err_prefix = J.status + c->max_chunks;
 }
 
 // Make sure scratch covers `chunks` chunks; (re)initialise the header.
@@ -83,20 +84,16 @@ int32_t ensure_scratch(gbu_ctx *c, uint64_t chunks, cudaStream_t stream)
         }
         c->max_chunks = want;
         if (!ok(cudaMemset(c->scratch, 0, kHeaderBytes + 16 * want))) return GBU_DEVICE_ERROR;
-        c->epoch = 0;
         c->dirty = true;
     }
     if (c->dirty) {
-        // claim = done = flags = 0, err = ~0
+        // claim = exit = flags = done = 0, first-error word = ~0, epoch = 0,
+        // and no status word may look ready
         static const uint64_t hdr[4] = {0, 0, ~0ull, 0};
-        if (!ok(cudaMemcpyAsync(c->scratch, hdr, sizeof hdr, cudaMemcpyHostToDevice, stream)))
+        if (!ok(cudaMemcpyAsync(c->scratch, hdr, sizeof hdr, cudaMemcpyHostToDevice, stream)) ||
+            !ok(cudaMemsetAsync(c->scratch + kHeaderBytes, 0, 8 * c->max_chunks, stream)))
             return GBU_DEVICE_ERROR;
         c->dirty = false;
-    }
-    if (++c->epoch > kEpochMask) {   // epoch wrap: clear the status words once
-        if (!ok(cudaMemsetAsync(c->scratch + kHeaderBytes, 0, 8 * c->max_chunks, stream)))
-            return GBU_DEVICE_ERROR;
-        c->epoch = 1;
     }
     return GBU_OK;
 }
@@ -116,28 +113,21 @@ int32_t enqueue(gbu_ctx *c, Op op, const void *in, uint64_t n, void *out, uint64
         g_launches.fetch_add(1, std::memory_order_relaxed);
         return ok(launch_write_result(dst, GBU_OK, 0, 0, stream)) ? GBU_OK : GBU_DEVICE_ERROR;
     }
-    Launch L{};
-    const void *base;
-    if (op == Op::U8toU16)
-        base = plan_utf8(static_cast<const uint8_t *>(in), n, L);
-    else
-        base = plan_utf16(static_cast<const uint16_t *>(in), n, L);
-    int32_t st = ensure_scratch(c, L.num_chunks, stream);
+    const bool utf16 = op == Op::U16toU8;
+    Job J{};
+    J.item0 = make_item(in, n, utf16, out, cap, write, dst, 0);
+    J.num_items = 1;
+    J.total_chunks = J.item0.nchunks;
+    int32_t st = ensure_scratch(c, J.total_chunks, stream);
     if (st != GBU_OK) {
         c->dirty = true;
         return st;
     }
-    L.s = scratch_of(c);
-    L.result = dst;
-    L.cap = write ? cap : 0;
-    L.epoch = c->epoch;
-    cudaError_t e;
-    if (op == Op::U8toU16)
-        e = launch_utf8_to_utf16(static_cast<const uint8_t *>(base), static_cast<uint16_t *>(out),
-                                 write, L, stream);
-    else
-        e = launch_utf16_to_utf8(static_cast<const uint16_t *>(base), static_cast<uint8_t *>(out),
-                                 write, L, stream);
+    attach_scratch(c, J);
+    int grid = job_max_grid(c->device);
+    if (grid <= 0) return GBU_DEVICE_ERROR;
+    if ((uint32_t)grid > J.total_chunks) grid = (int)J.total_chunks;
+    const cudaError_t e = launch_job(J, write, grid, stream);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     if (!ok(e)) {
         c->dirty = true;
@@ -207,7 +197,7 @@ int32_t gbu_reserve(gbu_ctx *c, uint64_t max_input_bytes)
 {
     if (!c) return GBU_INVALID_ARG;
     if (!ok(cudaSetDevice(c->device))) return GBU_DEVICE_ERROR;
-    const uint64_t chunks = (max_input_bytes + 16 + kChunk8 - 1) / kChunk8 + 1;
+    const uint64_t chunks = (max_input_bytes + 16 + kChunkBytes - 1) / kChunkBytes + 1;
     int32_t st = ensure_scratch(c, chunks, nullptr);
     if (st == GBU_OK && !ok(cudaDeviceSynchronize())) st = GBU_DEVICE_ERROR;
     return st;

@@ -1,14 +1,15 @@
-// Device-side machinery shared by the transcoding kernels: scratch layout,
-// block-wide scan, decoupled look-back over chunk status words, staged
-// coalesced stores, and the last-CTA result finalisation.
+// Device-side machinery shared by the transcoding kernel: job and item
+// descriptors, block-wide scan, decoupled look-back over chunk status words,
+// TMA bulk loads with mbarriers, staged coalesced stores, and per-item result
+// finalisation.
 //
 // The paper's transcoders advance sequentially by the n_in / n_out of each
 // 64-byte vector (Sec. 6.2, Eqs. for n_in and n_out; Sec. 7.3), and it sketches
 // the parallel alternative of computing each segment's transcoded size first
-// (Sec. 8, multithreading remark). On the GPU every chunk of the input is
-// transcoded by one CTA; the chunk's output offset is the exclusive prefix sum
-// of the output lengths of all earlier chunks, obtained in the same pass by a
-// decoupled look-back over per-chunk status words.
+// (Sec. 8, multithreading remark). On the GPU every chunk of an input is
+// transcoded by one CTA iteration; the chunk's output offset is the exclusive
+// prefix sum of the output lengths of the item's earlier chunks, obtained in
+// the same pass by a decoupled look-back over per-chunk status words.
 #pragma once
 
 #include <cstdint>
@@ -16,8 +17,47 @@
 
 namespace gbu {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 256;                 // compute threads of a CTA
+constexpr int kBlock = kThreads + 32;         // + one look-back warp
 constexpr unsigned kFull = 0xffffffffu;
+
+// Barrier among the kThreads compute threads only (named barrier 1), so the
+// look-back warp never takes part.
+__device__ __forceinline__ void cw_sync()
+{
+    asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory");
+}
+__device__ __forceinline__ bool cw_sync_or(bool v)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.or.pred p, 1, %2, q;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(kThreads)
+        : "memory");
+    return r != 0;
+}
+
+// Every chunk is 8 KiB of input in both directions: 8192 UTF-8 bytes or 4096
+// UTF-16 words. Thread t always owns input bytes [32t, 32t + 32) of its chunk.
+constexpr uint32_t kChunkBytes = 8192;
+constexpr uint32_t kChunk8 = kChunkBytes;        // UTF-8 bytes per chunk
+constexpr uint32_t kChunk16 = kChunkBytes / 2;   // UTF-16 words per chunk
+// Input ring: each stage holds one chunk plus kHalo bytes on each side.
+constexpr int kStages = 3;
+constexpr uint32_t kHalo = 16;
+constexpr uint32_t kStageBytes = kChunkBytes + 2 * kHalo;
+// Output staging capacity per chunk. UTF-8 -> UTF-16: at most one unit per
+// input byte, plus slack. UTF-16 -> UTF-8: a chunk's valid words need at most
+// 3 * kChunk16 + 1 bytes (3 per BMP word; a high surrogate that is the chunk's
+// last word adds 4 for 1). Offsets past an error may grow further; stores and
+// the write-out are bounded by these capacities (output past an error is
+// unspecified).
+constexpr uint32_t kStage8Units = kChunk8 + 8;
+constexpr uint32_t kStage16Bytes = 3 * kChunk16 + 8;
+constexpr uint32_t kOutBufBytes =
+    (2 * kStage8Units > kStage16Bytes ? 2 * kStage8Units : kStage16Bytes) + 16;
 
 // Status codes (numerically equal to gbu_status in include/gbutf.h).
 enum : int32_t {
@@ -34,8 +74,8 @@ constexpr uint64_t kFlagInclusive = 2;
 constexpr int kEpochShift = 40;
 constexpr uint32_t kEpochMask = (1u << 22) - 1;
 constexpr uint64_t kValueMask = (1ull << 40) - 1;
-// Bounded waits: a look-back poll gives up after this many rounds (each
-// round sleeps ~0.1-1 us), sets the timeout flag and lets the CTA finish.
+// Bounded waits: a poll loop gives up after this many rounds (each round
+// sleeps ~0.1-1 us), sets the timeout flag and lets the CTA finish.
 constexpr uint32_t kSpinLimit = 1u << 21;
 
 struct ResultSlot {      // layout of gbu_result
@@ -45,24 +85,36 @@ struct ResultSlot {      // layout of gbu_result
     uint64_t out_len;
 };
 
-struct Scratch {
-    unsigned int *claim;            // next chunk to hand out
-    unsigned int *done;             // CTAs finished
-    unsigned int *flags;            // bit 0: a bounded wait timed out; bit 1: bad chunk id
-    unsigned long long *err;        // (position << 8) | kind of the first error, ~0 if none
-    unsigned long long *status;     // [num_chunks] look-back words
-    unsigned long long *err_prefix; // [num_chunks] output units before the chunk's first error
+// One input of a job.
+enum : uint32_t { kOpUtf16 = 1u, kOpWrite = 2u };   // bit 0: input is UTF-16; bit 1: write output
+struct Item {
+    const uint8_t *in_al;   // 16-byte aligned base at or before the input
+    uint8_t *out;           // output (UTF-16 words or UTF-8 bytes)
+    uint64_t n;             // input units
+    uint64_t cap;           // output capacity in units (0 when nothing is written)
+    ResultSlot *result;     // device-visible result destination
+    uint32_t head;          // input units between in_al and the input
+    uint32_t op;            // kOpUtf16 | kOpWrite
+    uint32_t chunk_base;    // global index of the item's first chunk
+    uint32_t nchunks;       // chunks of this item (at least 1)
 };
 
-// Arguments common to every launch.
-struct Launch {
-    Scratch s;
-    ResultSlot *result;   // device-visible result destination
-    uint64_t n;           // input units
-    uint64_t cap;         // output capacity in units (ignored for length-only)
-    uint32_t head;        // input units between the 16-byte aligned base and the input
-    uint32_t num_chunks;
-    uint32_t epoch;
+// A job: one persistent launch over the chunks of one or more items.
+struct Job {
+    const Item *items;              // device array; nullptr: the single item `item0`
+    const uint32_t *chunk_item;     // per global chunk: its item (nullptr: item 0)
+    Item item0;
+    uint32_t num_items;
+    uint32_t total_chunks;
+    uint32_t status_capacity;       // status words in the scratch (cleared on epoch wrap)
+    unsigned int *epoch;            // launch epoch: read at start, advanced by the last CTA
+    unsigned int *claim;            // next chunk to hand out
+    unsigned int *exit_count;       // CTAs that left the chunk loop
+    unsigned int *flags;            // bit 0: a bounded wait timed out; bit 1: bad chunk id
+    unsigned long long *status;     // [total_chunks] look-back words
+    unsigned long long *err_prefix; // [total_chunks] output units before the chunk's first error
+    unsigned long long *item_err;   // [num_items] (position << 8) | kind of the first error, ~0 if none
+    unsigned int *item_done;        // [num_items] chunks written
 };
 
 __device__ __forceinline__ uint64_t ld_relaxed(const unsigned long long *p)
@@ -89,7 +141,7 @@ __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v)
     return v;
 }
 
-// Block-wide exclusive scan of one uint32 per thread (kThreads threads).
+// Exclusive scan of one uint32 per compute thread (kThreads threads).
 // Returns the thread's exclusive prefix; *total receives the block sum.
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *warp_tot,
                                                          uint32_t *total)
@@ -102,7 +154,7 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *w
         if (lane >= o) inc += t;
     }
     if (lane == 31) warp_tot[warp] = inc;
-    __syncthreads();
+    cw_sync();
     if (warp == 0) {
         uint32_t w = lane < kThreads / 32 ? warp_tot[lane] : 0;
         uint32_t wi = w;
@@ -114,52 +166,84 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *w
         if (lane < kThreads / 32) warp_tot[lane] = wi - w;   // exclusive warp base
         if (lane == kThreads / 32 - 1) warp_tot[kThreads / 32] = wi;
     }
-    __syncthreads();
+    cw_sync();
     *total = warp_tot[kThreads / 32];
     return warp_tot[warp] + inc - v;
 }
 
-// Decoupled look-back, run by one full warp of the CTA that owns `chunk`
-// (chunk > 0). Reads up to 32 predecessors at a time; sums aggregates back
-// to the nearest inclusive prefix. Returns the chunk's exclusive prefix (all
-// lanes). On a wait longer than kSpinLimit rounds it sets the timeout flag
-// and returns what it has.
-__device__ __forceinline__ uint64_t lookback(const Launch &L, uint32_t chunk)
+// Decoupled look-back, run by one full warp for the item chunk `k` (k > 0)
+// whose status words start at `status` (the item's first chunk). Each round
+// reads kLookWidth words per lane (the 32 * kLookWidth nearest predecessors
+// not yet summed) in one L2 round trip, sums aggregates back to the nearest
+// inclusive prefix, and moves on if there is none. Returns the chunk's
+// exclusive prefix (all lanes). On a wait longer than kSpinLimit polls, or as
+// soon as another CTA of the launch gave up, it sets the timeout flag and
+// returns what it has.
+#ifndef GBU_LOOK_WIDTH
+#define GBU_LOOK_WIDTH 8
+#endif
+constexpr int kLookWidth = GBU_LOOK_WIDTH;
+
+__device__ __forceinline__ uint64_t lookback(const unsigned long long *status, uint32_t k,
+                                             uint32_t epoch, unsigned int *flags)
 {
     const int lane = threadIdx.x & 31;
     uint64_t excl = 0;
-    int64_t base = (int64_t)chunk - 1;
+    int64_t base = (int64_t)k - 1;
     uint32_t rounds = 0;
     while (true) {
-        const int64_t idx = base - lane;
-        uint64_t val = 0, flag = kFlagInclusive;   // before chunk 0: inclusive 0
+        uint64_t val[kLookWidth];
+        uint32_t inc[kLookWidth], nr[kLookWidth];
         while (true) {
-            if (idx >= 0) {
-                const uint64_t w = ld_relaxed(&L.s.status[idx]);
-                flag = w >> 62;
-                if (((w >> kEpochShift) & kEpochMask) != L.epoch) flag = 0;
-                val = w & kValueMask;
+#pragma unroll
+            for (int m = 0; m < kLookWidth; m++) {
+                const int64_t idx = base - 32 * m - lane;
+                uint64_t flag = kFlagInclusive;   // before the item's first chunk: inclusive 0
+                val[m] = 0;
+                if (idx >= 0) {
+                    const uint64_t w = ld_relaxed(&status[idx]);
+                    flag = w >> 62;
+                    if (((w >> kEpochShift) & kEpochMask) != epoch) flag = 0;
+                    val[m] = w & kValueMask;
+                }
+                inc[m] = __ballot_sync(kFull, flag == kFlagInclusive);
+                nr[m] = __ballot_sync(kFull, flag == 0);
             }
-            if (__all_sync(kFull, flag != 0)) break;
+            // ready when no word before the nearest inclusive one is missing
+            bool ready = true, found = false;
+#pragma unroll
+            for (int m = 0; m < kLookWidth; m++) {
+                if (found) break;
+                const uint32_t upto = inc[m] ? ((inc[m] & (0u - inc[m])) - 1u) : 0xFFFFFFFFu;
+                if (nr[m] & upto) ready = false;
+                if (inc[m]) found = true;
+            }
+            if (ready) break;
             ++rounds;
-            // give up after kSpinLimit rounds, or at once when another CTA
-            // of this launch already gave up
             const bool other = (rounds & 63u) == 0 &&
-                               *reinterpret_cast<volatile unsigned int *>(L.s.flags) != 0;
+                               *reinterpret_cast<volatile unsigned int *>(flags) != 0;
             if (rounds > kSpinLimit || __any_sync(kFull, other)) {
-                if (lane == 0) atomicOr(L.s.flags, 1u);
+                if (lane == 0) atomicOr(flags, 1u);
                 return excl;
             }
             __nanosleep(rounds < 8 ? 32 : 256);
         }
-        const uint32_t inc = __ballot_sync(kFull, flag == kFlagInclusive);
-        if (inc) {
-            const int l = __ffs(inc) - 1;    // nearest predecessor with a full prefix
-            excl += warp_sum_u64(lane <= l ? val : 0);
-            return excl;
+        uint64_t part = 0;
+        bool found = false;
+#pragma unroll
+        for (int m = 0; m < kLookWidth; m++) {
+            if (found) break;
+            if (inc[m]) {
+                const int l = __ffs(inc[m]) - 1;    // nearest predecessor with a full prefix
+                if (lane <= l) part += val[m];
+                found = true;
+            } else {
+                part += val[m];
+            }
         }
-        excl += warp_sum_u64(val);
-        base -= 32;
+        excl += warp_sum_u64(part);
+        if (found) return excl;
+        base -= 32 * kLookWidth;
     }
 }
 
@@ -193,7 +277,7 @@ __device__ __forceinline__ void block_store_bytes(const uint8_t *s_src, uint8_t 
 }
 
 // Zero the bytes of a 32-bit little-endian word whose virtual positions
-// (vpos .. vpos+3) fall outside [lo, hi).
+// (vpos .. vpos+3, in bytes) fall outside [lo, hi).
 __device__ __forceinline__ uint32_t mask_word_bytes(uint32_t w, int64_t vpos, int64_t lo, int64_t hi)
 {
     uint32_t keep = 0;
@@ -203,67 +287,12 @@ __device__ __forceinline__ uint32_t mask_word_bytes(uint32_t w, int64_t vpos, in
     return w & keep;
 }
 
-// End of a launch, called by thread 0 of every CTA after its last status /
-// error-word writes: count the CTA done; the last one assembles the
-// gbu_result from the scan total and the first-error word, stores it, and
-// resets the counters for the next launch on this scratch. Only the scan and
-// error words need ordering before the done count (the output itself is not
-// read by the finisher), so one thread fences, not the whole CTA.
-template <bool kWrite>
-__device__ __forceinline__ void finish_launch(const Launch &L, uint32_t chunk_elems)
-{
-    __threadfence();
-    if (atomicAdd(L.s.done, 1u) != gridDim.x - 1) return;
-    __threadfence();
-    const uint64_t total = ld_relaxed(&L.s.status[L.num_chunks - 1]) & kValueMask;
-    const uint64_t err = ld_relaxed(L.s.err);
-    const unsigned int flags = atomicAdd(L.s.flags, 0u);
-    int32_t st;
-    uint64_t off, len;
-    if (flags & 2u) {
-        st = kDeviceError; off = 0; len = 0;
-    } else if (flags & 1u) {
-        st = kDeviceTimeout; off = 0; len = 0;
-    } else if (err != ~0ull) {
-        st = (int32_t)(err & 0xFF);
-        off = err >> 8;
-        const uint64_t c = (off + L.head) / chunk_elems;
-        len = ld_relaxed(&L.s.err_prefix[c]);
-    } else {
-        st = (kWrite && total > L.cap) ? kOutputTooSmall : kOk;
-        off = L.n;
-        len = total;
-    }
-    volatile ResultSlot *r = L.result;
-    r->status = st;
-    r->reserved = 0;
-    r->in_offset = off;
-    r->out_len = len;
-    *L.s.claim = 0;
-    *L.s.done = 0;
-    *L.s.flags = 0;
-    st_relaxed(L.s.err, ~0ull);
-    __threadfence_system();
-}
-
 // First-error key inside a CTA: position (39 bits) | kind (8 bits) | output
 // units of the chunk before the error (15 bits). Positions are unique, so the
 // minimum key is the first error and carries its prefix length along.
 __device__ __forceinline__ uint64_t err_key(uint64_t pos, uint32_t kind, uint32_t units)
 {
     return (pos << 23) | ((uint64_t)kind << 15) | (units & 0x7FFFu);
-}
-
-// Thread 0, after the look-back: publish the chunk's first error (if any)
-// into the per-chunk prefix slot and the grid-wide first-error word.
-__device__ __forceinline__ void publish_error(const Launch &L, uint32_t chunk, uint64_t key,
-                                              uint64_t excl)
-{
-    if (key == ~0ull) return;
-    const uint64_t pos = key >> 23;
-    const uint32_t kind = (uint32_t)(key >> 15) & 0xFFu;
-    L.s.err_prefix[chunk] = excl + (key & 0x7FFFu);
-    atomicMin(L.s.err, (pos << 8) | kind);
 }
 
 // PTX prmt.b32 (generic mode): byte k of the result is byte sel[4k+2:4k] of
@@ -277,13 +306,126 @@ __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel)
     return d;
 }
 
-// Byte-wise helpers on little-endian 32-bit words holding 4 input bytes.
 // zero_bytes(v): bit 7 of every byte of v that is zero. Exact when no byte of
 // v can be 0x01 directly above a zero byte (callers pass values whose bytes
 // are even or multiples of 0x10); otherwise a superset, used only for flags.
 __device__ __forceinline__ uint32_t zero_bytes(uint32_t v)
 {
     return (v - 0x01010101u) & ~v & 0x80808080u;
+}
+
+// ---- mbarrier + TMA bulk copy (PTX) -------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
+            smem_u32(bar)),
+        "r"(bytes)
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for a phase of an mbarrier; false when the wait gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    for (uint32_t i = 0; i < kSpinLimit; i++) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (i > 16) __nanosleep(64);
+    }
+    return false;
+}
+
+// Order earlier generic-proxy accesses of shared memory before later
+// async-proxy (TMA) accesses by this thread.
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// 1-D TMA bulk copy global -> shared, completing `bytes` on `bar`. Both
+// addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t bytes,
+                                            uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// ---- per-item result ------------------------------------------------------
+
+// One thread, after the item's last chunk was written: assemble the
+// gbu_result from the scan total and the first-error word, store it, and reset
+// the item's counters for the next launch.
+__device__ __forceinline__ void finalize_item(const Job &J, uint32_t it, const Item &I)
+{
+    __threadfence();
+    const uint64_t total =
+        ld_relaxed(&J.status[I.chunk_base + I.nchunks - 1]) & kValueMask;
+    const uint64_t err = ld_relaxed(&J.item_err[it]);
+    const unsigned int flags = atomicAdd(J.flags, 0u);
+    const uint32_t chunk_units = (I.op & kOpUtf16) ? kChunk16 : kChunk8;
+    int32_t st;
+    uint64_t off, len;
+    if (flags & 2u) {
+        st = kDeviceError; off = 0; len = 0;
+    } else if (flags & 1u) {
+        st = kDeviceTimeout; off = 0; len = 0;
+    } else if (err != ~0ull) {
+        st = (int32_t)(err & 0xFF);
+        off = err >> 8;
+        const uint64_t c = I.chunk_base + (off + I.head) / chunk_units;
+        len = ld_relaxed(&J.err_prefix[c]);
+    } else {
+        st = ((I.op & kOpWrite) && total > I.cap) ? kOutputTooSmall : kOk;
+        off = I.n;
+        len = total;
+    }
+    volatile ResultSlot *r = I.result;
+    r->status = st;
+    r->reserved = 0;
+    r->in_offset = off;
+    r->out_len = len;
+    J.item_done[it] = 0;
+    st_relaxed(&J.item_err[it], ~0ull);
+    __threadfence_system();
 }
 
 }  // namespace gbu

@@ -1,4 +1,4 @@
-// Host-side launch functions for the transcoding kernels (internal).
+// Host-side view of the transcoding kernel (internal).
 #pragma once
 
 #include <cstdint>
@@ -6,21 +6,30 @@
 
 #include "common.cuh"
 
+// Resident CTAs per SM the kernel is compiled for (register budget).
+#ifndef GBU_MIN_BLOCKS
+#define GBU_MIN_BLOCKS 3
+#endif
+
 namespace gbu {
 
-// Input units per chunk (one CTA iteration) for each direction.
-constexpr uint32_t kChunk8 = 8192;    // UTF-8 bytes per chunk
-constexpr uint32_t kChunk16 = 4096;   // UTF-16 words per chunk
+constexpr int kMinBlocks = GBU_MIN_BLOCKS;
 
-// Fill in L.head / L.num_chunks for an input pointer and size; returns the
-// 16-byte aligned base the kernels read from.
-const uint8_t *plan_utf8(const uint8_t *in, uint64_t n, Launch &L);
-const uint16_t *plan_utf16(const uint16_t *in, uint64_t n, Launch &L);
+// Scratch header shared by every job launch on one scratch area.
+constexpr size_t kHdrClaim = 0, kHdrExit = 4, kHdrFlags = 8, kHdrDone = 12, kHdrErr = 16,
+                 kHdrEpoch = 24;
+constexpr size_t kHdrResult = 64;   // result slot (used where no caller slot exists)
+constexpr size_t kHeaderBytes = 256;
 
-cudaError_t launch_utf8_to_utf16(const uint8_t *in_aligned, uint16_t *out, bool write,
-                                 const Launch &L, cudaStream_t stream);
-cudaError_t launch_utf16_to_utf8(const uint16_t *in_aligned, uint8_t *out, bool write,
-                                 const Launch &L, cudaStream_t stream);
+// Describe one input (chunk count included) for a job starting at chunk_base.
+Item make_item(const void *in, uint64_t n, bool utf16, void *out, uint64_t cap, bool write,
+               ResultSlot *result, uint32_t chunk_base);
+
+// Dynamic shared memory of one CTA; grid size that keeps every CTA resident.
+size_t job_smem_bytes(bool write);
+int job_max_grid(int device);
+
+cudaError_t launch_job(const Job &J, bool write, int grid, cudaStream_t stream);
 cudaError_t launch_write_result(ResultSlot *dst, int32_t status, uint64_t in_offset,
                                 uint64_t out_len, cudaStream_t stream);
 

@@ -28,16 +28,14 @@ using namespace gbu;
 
 namespace {
 
-constexpr uint64_t kNoAllocChunks = (GBU_NOALLOC_MAX_BYTES + 15 + kChunk8 - 1) / kChunk8;
-constexpr size_t kHeader = 256;   // claim, done, flags | err | result slot | spare
-constexpr size_t kScratchBytes = kHeader + 16 * kNoAllocChunks;
+constexpr uint64_t kNoAllocChunks = (GBU_NOALLOC_MAX_BYTES + 15 + kChunkBytes - 1) / kChunkBytes;
+constexpr size_t kScratchBytes = kHeaderBytes + 16 * kNoAllocChunks;
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 struct DeviceState {
     unsigned char *base = nullptr;   // device address of g_noalloc_scratch
-    uint32_t epoch = 0;
 };
 
 std::mutex g_mu;
@@ -71,9 +69,13 @@ extern "C" gbu_result gbu_utf8_to_utf16le_noalloc(const uint8_t *d_in, uint64_t 
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
         return fail(GBU_DEVICE_ERROR);
 
-    Launch L{};
-    const uint8_t *base_in = plan_utf8(d_in, n_bytes, L);
-    if (L.num_chunks > kNoAllocChunks) return fail(GBU_INVALID_ARG);
+    Job J{};
+    J.item0 = make_item(d_in, n_bytes, false, d_out, cap_units, true, nullptr, 0);
+    J.num_items = 1;
+    J.total_chunks = J.item0.nchunks;
+    if (J.total_chunks > kNoAllocChunks) return fail(GBU_INVALID_ARG);
+    const int max_grid = job_max_grid(dev);
+    if (max_grid <= 0) return fail(GBU_DEVICE_ERROR);
 
     unsigned char *base;
     {
@@ -83,19 +85,12 @@ extern "C" gbu_result gbu_utf8_to_utf16le_noalloc(const uint8_t *d_in, uint64_t 
             void *p = nullptr;
             if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p)
                 return fail(GBU_DEVICE_ERROR);
-            // status words must start "not ready" for every epoch
+            // status words must start "not ready"; the kernel keeps the epoch
             if (cudaMemsetAsync(p, 0, kScratchBytes, s) != cudaSuccess)
                 return fail(GBU_DEVICE_ERROR);
             d.base = static_cast<unsigned char *>(p);
-            d.epoch = 0;
-        }
-        if (++d.epoch > kEpochMask) {   // epoch wrap: clear the status words once
-            if (cudaMemsetAsync(d.base + kHeader, 0, 8 * kNoAllocChunks, s) != cudaSuccess)
-                return fail(GBU_DEVICE_ERROR);
-            d.epoch = 1;
         }
         base = d.base;
-        L.epoch = d.epoch;
     }
     // The array keeps whatever the previous call left: counters and flags must
     // start at zero and the first-error word at all ones.
@@ -103,18 +98,20 @@ extern "C" gbu_result gbu_utf8_to_utf16le_noalloc(const uint8_t *d_in, uint64_t 
         cudaMemsetAsync(base + 16, 0xFF, 8, s) != cudaSuccess)
         return fail(GBU_DEVICE_ERROR);
 
-    L.s.claim = reinterpret_cast<unsigned int *>(base);
-    L.s.done = L.s.claim + 1;
-    L.s.flags = L.s.claim + 2;
-    L.s.err = reinterpret_cast<unsigned long long *>(base + 16);
-    L.s.status = reinterpret_cast<unsigned long long *>(base + kHeader);
-    L.s.err_prefix = L.s.status + kNoAllocChunks;
-    L.result = reinterpret_cast<ResultSlot *>(base + 64);
-    L.cap = cap_units;
-    if (launch_utf8_to_utf16(base_in, d_out, true, L, s) != cudaSuccess)
-        return fail(GBU_DEVICE_ERROR);
+    J.claim = reinterpret_cast<unsigned int *>(base + kHdrClaim);
+    J.exit_count = reinterpret_cast<unsigned int *>(base + kHdrExit);
+    J.flags = reinterpret_cast<unsigned int *>(base + kHdrFlags);
+    J.item_done = reinterpret_cast<unsigned int *>(base + kHdrDone);
+    J.item_err = reinterpret_cast<unsigned long long *>(base + kHdrErr);
+    J.epoch = reinterpret_cast<unsigned int *>(base + kHdrEpoch);
+    J.status = reinterpret_cast<unsigned long long *>(base + kHeaderBytes);
+    J.status_capacity = (uint32_t)kNoAllocChunks;
+    J.err_prefix = J.status + kNoAllocChunks;
+    J.item0.result = reinterpret_cast<ResultSlot *>(base + kHdrResult);
+    const int grid = (uint32_t)max_grid > J.total_chunks ? (int)J.total_chunks : max_grid;
+    if (launch_job(J, true, grid, s) != cudaSuccess) return fail(GBU_DEVICE_ERROR);
     gbu_result r;
-    if (cudaMemcpyAsync(&r, base + 64, sizeof r, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+    if (cudaMemcpyAsync(&r, base + kHdrResult, sizeof r, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
         return fail(GBU_DEVICE_ERROR);
     return r;

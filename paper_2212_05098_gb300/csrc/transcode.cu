@@ -1,0 +1,827 @@
+// Persistent, validating UTF-8 <-> UTF-16LE transcoding kernel (paper Sec. 6
+// and Sec. 7) over a job of one or more inputs.
+//
+// Work decomposition. Every input ("item") is cut into 8 KiB chunks; the
+// chunks of all items of a job are numbered globally and handed out in order
+// by an atomic counter. A persistent grid (a few CTAs per SM) loops over them:
+//   * thread 0 claims chunks ahead and loads each one, with 16 bytes of
+//     context on either side, into a ring of kStages shared-memory stages by
+//     a 1-D TMA bulk copy completing on the stage's mbarrier;
+//   * the 256 threads classify the chunk (thread t owns bytes [32t, 32t+32)),
+//     count its output, scan the counts across the CTA and publish the
+//     chunk's aggregate for the decoupled look-back;
+//   * the compute threads then assemble the chunk's output into one of two
+//     shared-memory staging buffers;
+//   * a ninth warp looks back for each chunk's offset as soon as its
+//     aggregate is out, waits for the staged output, writes it with 16-byte
+//     stores and frees the buffer.
+// The compute warps thus never wait on a look-back (only on input and on a
+// free staging buffer), and the TMA ring keeps two chunks of input in flight
+// per CTA.
+//
+// Ownership: a UTF-8 unit belongs to the thread holding its end position
+// (see chunk8 below); a UTF-16 surrogate pair belongs to the owner of its
+// high surrogate. Errors are located by the exact local rules described with
+// each chunk body; the minimum (position, kind) over a chunk and then over
+// the item is the sequential decoder's first error (the paper's ell).
+#include "kernels.h"
+
+namespace gbu {
+
+namespace {
+
+constexpr uint32_t kB7 = 0x80808080u;
+
+// ===========================================================================
+// UTF-8 -> UTF-16LE chunk (paper Sec. 6)
+//
+// Classification (Sec. 6.1) four bytes at a time: indicator bit 7 of each
+// byte for "continuation" (80-BF), ">= C0", ">= E0" and ">= F0" (the
+// complement of the paper's m_1234, and m_234, m_34, m_4).
+//
+// Units are produced at the end positions of the sequences, as in the paper
+// (Sec. 6.1-6.2): every last byte of a character, and the third byte of a
+// 4-byte character, ends one UTF-16 unit, assembled from the last, second last
+// and third last bytes with their tag bits stripped,
+//   W = W_-2 << 12 | W_-1 << 6 | W_end   (Eq. W_sum, 16-bit),
+// where W_-1 is used when the end byte is not ASCII and W_-2 when the byte two
+// back is a 3/4-byte lead; high surrogates become (W >> 4) + 0xD7C0 and low
+// surrogates W | 0xDC00 (Eq. W_out). Four end positions are assembled at once
+// on two registers of 16-bit lanes. A position p is an end when the byte after
+// it does not continue a sequence, or when it is the third byte of a 4-byte
+// sequence; "continues" means a continuation byte that a lead at p-1, p-2 or
+// p-3 expects (the paper's m_c), so a stray continuation byte also ends the
+// valid prefix before it and the units of the valid prefix stay exact in a
+// chunk that holds an error. Each position ends at most one unit.
+//
+// Validation (Sec. 6.4), two levels:
+//  * fast, every thread: the structure check is exact (expected continuation
+//    positions must equal the continuation positions: rules 2-3); bad bytes
+//    and out-of-range values (rules 1, 4-6: C0/C1, F5-FF, E0+80..9F,
+//    ED+A0..BF, F0+80..8F, F4+90..BF) are caught by a check that never misses
+//    an error but may flag a valid word (its E0/ED and F0/F4/F5+ parts run
+//    only in warps holding such bytes);
+//  * exact, only in flagged threads: for every position p the rule the
+//    sequential decoder applies if a character starts at p (stray
+//    continuation -> TOO_LONG; C0/C1 -> OVERLONG; F5-FF -> HEADER_BITS; lead
+//    without its continuations -> TOO_SHORT; then OVERLONG / SURROGATE /
+//    TOO_LARGE from the value). The smallest such p is exactly where the
+//    sequential decoder stops: every earlier position is a validated character
+//    start or a continuation inside one.
+// ===========================================================================
+
+struct Cls {
+    uint32_t c2, c3, c4, ct;   // bit 7 of each byte: >= C0, >= E0, >= F0, 80-BF
+};
+
+__device__ __forceinline__ Cls classify(uint32_t x)
+{
+    const uint32_t x1 = x << 1;
+    Cls c;
+    c.c2 = x & x1 & kB7;
+    c.c3 = c.c2 & (x << 2);
+    c.c4 = c.c3 & (x << 3);
+    c.ct = x & ~x1 & kB7;
+    return c;
+}
+
+// byte k of the result = byte k-n/8 of the 64-bit (cur:prev) (values n bytes back)
+__device__ __forceinline__ uint32_t back(uint32_t prev, uint32_t cur, int n)
+{
+    return __funnelshift_l(prev, cur, n);
+}
+// byte k of the result = byte k+n/8 of (next:cur) (values n bytes ahead)
+__device__ __forceinline__ uint32_t ahead(uint32_t cur, uint32_t next, int n)
+{
+    return __funnelshift_r(cur, next, n);
+}
+
+// 4 bits of a position mask -> bit 7 of the 4 bytes of a word.
+__device__ __forceinline__ uint32_t spread4(uint32_t m4)
+{
+    return ((m4 * 0x00204081u) & 0x01010101u) << 7;
+}
+
+// Exact local rule for every owned position of a flagged thread (rare path).
+// w: 10 words (positions -4 .. 35); end: the 8 end-indicator words. Returns
+// the key of the first error, or ~0.
+__device__ __noinline__ uint64_t first_error_exact8(const uint32_t *w, const uint32_t *end,
+                                                    uint32_t vmask, int64_t pos0, uint32_t t_off)
+{
+    uint32_t units = 0;
+    for (int i = 0; i < 32; i++) {
+        const int j = (i >> 2) + 1;
+        const int sh = (i & 3) * 8;
+        const uint32_t xf = __funnelshift_r(w[j], w[j + 1], sh);   // bytes i .. i+3
+        const uint32_t xb = __funnelshift_r(w[j - 1], w[j], sh);   // bytes i-4 .. i-1
+        const uint32_t b0 = xf & 0xFFu;
+        int kind = 0;
+        if ((b0 & 0xC0u) == 0x80u) {
+            const uint32_t p1 = xb >> 24, p2 = (xb >> 16) & 0xFFu, p3 = (xb >> 8) & 0xFFu;
+            if (!(p1 >= 0xC0u || p2 >= 0xE0u || p3 >= 0xF0u)) kind = kTooLong;
+        } else if (b0 >= 0x80u) {
+            if (b0 < 0xC2u) {
+                kind = kOverlong;
+            } else if (b0 >= 0xF5u) {
+                kind = kHeaderBits;
+            } else {
+                const uint32_t len = b0 < 0xE0u ? 2u : (b0 < 0xF0u ? 3u : 4u);
+                const uint32_t c = (xf ^ 0x80808080u) & 0xC0C0C0C0u;   // zero byte: continuation
+                const uint32_t need = len == 2 ? 0x0000FF00u : (len == 3 ? 0x00FFFF00u : 0xFFFFFF00u);
+                if (c & need) {
+                    kind = kTooShort;
+                } else {
+                    const uint32_t b1 = (xf >> 8) & 0x3Fu, b2 = (xf >> 16) & 0x3Fu;
+                    const uint32_t b3 = (xf >> 24) & 0x3Fu;
+                    uint32_t cp;
+                    if (len == 2) cp = ((b0 & 0x1Fu) << 6) | b1;
+                    else if (len == 3) cp = ((b0 & 0x0Fu) << 12) | (b1 << 6) | b2;
+                    else cp = ((b0 & 0x07u) << 18) | (b1 << 12) | (b2 << 6) | b3;
+                    if (len == 3 && cp < 0x800u) kind = kOverlong;
+                    else if (len == 3 && (cp & 0xF800u) == 0xD800u) kind = kSurrogate;
+                    else if (len == 4 && cp < 0x10000u) kind = kOverlong;
+                    else if (len == 4 && cp > 0x10FFFFu) kind = kTooLarge;
+                }
+            }
+        }
+        if (kind != 0 && ((vmask >> i) & 1u)) return err_key((uint64_t)(pos0 + i), kind, t_off + units);
+        units += (end[i >> 2] >> (8 * (i & 3) + 7)) & 1u;
+    }
+    return ~0ull;
+}
+
+struct St8 {
+    uint32_t w[10];    // w[0]: bytes -4..-1, w[1..8]: own bytes 0..31, w[9]: 32..35
+    uint32_t end[8];   // end-position indicators (bit 7 of each byte)
+    uint32_t vmask;    // owned positions inside the input
+    uint32_t bad;      // the fast check fired
+    bool edge, warp3, warp4;
+};
+
+// Load, classify, check structure, count units. Returns the thread's count.
+__device__ __forceinline__ uint32_t chunk8_phase1(St8 &st, const uint8_t *stage, int64_t vt,
+                                                  int64_t lo, int64_t hi)
+{
+    const uint8_t *sp = stage + kHalo + 32 * threadIdx.x;
+    const uint4 a = *reinterpret_cast<const uint4 *>(sp);
+    const uint4 b = *reinterpret_cast<const uint4 *>(sp + 16);
+    uint32_t *w = st.w;
+    w[1] = a.x; w[2] = a.y; w[3] = a.z; w[4] = a.w;
+    w[5] = b.x; w[6] = b.y; w[7] = b.z; w[8] = b.w;
+    w[0] = *reinterpret_cast<const uint32_t *>(sp - 4);
+    w[9] = *reinterpret_cast<const uint32_t *>(sp + 32);
+    st.vmask = 0xFFFFFFFFu;
+    st.edge = vt < lo || vt + 32 > hi;
+    if (st.edge) {   // input edges only
+        st.vmask = 0;
+#pragma unroll
+        for (int i = 0; i < 32; i++)
+            if (vt + i >= lo && vt + i < hi) st.vmask |= 1u << i;
+#pragma unroll
+        for (int j = 0; j < 8; j++) w[1 + j] = mask_word_bytes(w[1 + j], vt + 4 * j, lo, hi);
+    }
+    if (vt - 4 < lo || vt + 36 > hi) {
+        w[0] = mask_word_bytes(w[0], vt - 4, lo, hi);
+        w[9] = mask_word_bytes(w[9], vt + 32, lo, hi);
+    }
+
+    uint32_t bad = 0, any3, any4, cnt = 0;
+    {
+        Cls cl[10];
+#pragma unroll
+        for (int j = 0; j < 10; j++) cl[j] = classify(w[j]);
+        // leads in the look-behind word shape the units at the first positions
+        any3 = cl[0].c3;
+        any4 = cl[0].c4;
+        uint32_t ec[9];
+#pragma unroll
+        for (int j = 1; j <= 8; j++) {
+            const uint32_t exp = back(cl[j - 1].c2, cl[j].c2, 8) | back(cl[j - 1].c3, cl[j].c3, 16) |
+                                 back(cl[j - 1].c4, cl[j].c4, 24);
+            bad |= exp ^ cl[j].ct;
+            ec[j - 1] = exp & cl[j].ct;
+            // C0 / C1: 2-byte leads whose bits 4..1 are zero
+            bad |= cl[j].c2 & ~cl[j].c3 & zero_bytes(w[j] & 0x1E1E1E1Eu);
+            any3 |= cl[j].c3;
+            any4 |= cl[j].c4;
+        }
+        // continuations the last leads expect at positions 32..34
+        const uint32_t exp9 = (cl[8].c2 >> 24) | (cl[8].c3 >> 16) | (cl[8].c4 >> 8);
+        bad |= exp9 & ~cl[9].ct;
+        ec[8] = exp9 & cl[9].ct;
+#pragma unroll
+        for (int j = 1; j <= 8; j++) {
+            uint32_t e = (~ahead(ec[j - 1], ec[j], 8) | back(cl[j - 1].c4, cl[j].c4, 16)) & kB7;
+            if (st.edge) e &= spread4((st.vmask >> (4 * (j - 1))) & 0xFu);
+            st.end[j - 1] = e;
+            cnt += __popc(e);
+        }
+    }
+    st.warp3 = __any_sync(kFull, any3 != 0);
+    st.warp4 = __any_sync(kFull, any4 != 0);
+    if (st.warp3) {
+        // E0 + 80..9F (overlong), ED + A0..BF (surrogate); may over-flag
+#pragma unroll
+        for (int j = 1; j <= 8; j++) {
+            const uint32_t y5 = ahead(w[j], w[j + 1], 8) << 2;   // bit 5 of the next byte
+            bad |= zero_bytes(w[j] ^ 0xE0E0E0E0u) & ~y5;
+            bad |= zero_bytes(w[j] ^ 0xEDEDEDEDu) & y5;
+        }
+    }
+    if (st.warp4) {
+        // F0 + 80..8F (overlong), F4 + 90..BF (too large), F5..FF; may over-flag
+#pragma unroll
+        for (int j = 1; j <= 8; j++) {
+            const uint32_t y = ahead(w[j], w[j + 1], 8);
+            const uint32_t y54 = (y << 2) | (y << 3);              // bits 5 or 4 of the next byte
+            bad |= zero_bytes(w[j] ^ 0xF0F0F0F0u) & ~y54;
+            bad |= zero_bytes(w[j] ^ 0xF4F4F4F4u) & y54;
+            bad |= classify(w[j]).c4 & (((w[j] & 0x0F0F0F0Fu) + 0x0B0B0B0Bu) << 3);
+        }
+    }
+    st.bad = bad;
+    return cnt;
+}
+
+// Exact first error (flagged threads) and staging of the units.
+template <bool kWrite>
+__device__ __forceinline__ void chunk8_phase2(St8 &st, uint8_t *obuf, uint32_t t_off, int64_t vt,
+                                              int64_t lo, unsigned long long *s_err)
+{
+    if (st.bad || st.edge) {
+        const uint64_t key = first_error_exact8(st.w, st.end, st.vmask, vt - lo, t_off);
+        if (key != ~0ull) atomicMin(s_err, key);
+    }
+    if (!kWrite) return;
+    const uint32_t *w = st.w;
+    uint32_t s[9], c3[9], c4[9];
+#pragma unroll
+    for (int j = 0; j < 9; j++) {
+        const Cls c = classify(w[j]);
+        c3[j] = c.c3;
+        c4[j] = c.c4;
+        const uint32_t na = prmt(w[j], 0, 0xBA98);        // 0xFF where byte >= 0x80
+        s[j] = w[j] & ~(na & 0xC0C0C0C0u);                // tag bits stripped
+    }
+    uint16_t *p = reinterpret_cast<uint16_t *>(obuf) + t_off;
+#pragma unroll
+    for (int j = 1; j <= 8; j++) {
+        const uint32_t na = prmt(w[j], 0, 0xBA98);
+        const uint32_t s1 = back(s[j - 1], s[j], 8) & na;          // W_-1 where end byte is not ASCII
+        uint32_t wa = prmt(s[j], 0, 0x4140) + (prmt(s1, 0, 0x4140) << 6);
+        uint32_t wb = prmt(s[j], 0, 0x4342) + (prmt(s1, 0, 0x4342) << 6);
+        if (st.warp3) {
+            // W_-2 (low 4 bits) where the byte two back is a 3/4-byte lead
+            const uint32_t m3 = prmt(c3[j - 1], c3[j], 0xDCBA);
+            const uint32_t s2 = back(s[j - 1], s[j], 16) & m3 & 0x0F0F0F0Fu;
+            wa += prmt(s2, 0, 0x4140) << 12;
+            wb += prmt(s2, 0, 0x4342) << 12;
+        }
+        if (st.warp4) {
+            // surrogates: high at the third byte of a 4-byte sequence,
+            // low at its fourth byte (Eq. W_out)
+            const uint32_t hma = prmt(c4[j - 1], c4[j], 0xBBAA);
+            const uint32_t hmb = prmt(c4[j - 1], c4[j], 0xDDCC);
+            const uint32_t lma = prmt(c4[j - 1], c4[j], 0xAA99);
+            const uint32_t lmb = prmt(c4[j - 1], c4[j], 0xCCBB);
+            const uint32_t ha = ((wa >> 4) & 0x0FFF0FFFu) + 0xD7C0D7C0u;
+            const uint32_t hb = ((wb >> 4) & 0x0FFF0FFFu) + 0xD7C0D7C0u;
+            wa = ((ha & hma) | (wa & ~hma)) | (lma & 0xDC00DC00u);
+            wb = ((hb & hmb) | (wb & ~hmb)) | (lmb & 0xDC00DC00u);
+        }
+        const uint32_t e = st.end[j - 1];
+        if (e & 0x00000080u) *p++ = (uint16_t)wa;
+        if (e & 0x00008000u) *p++ = (uint16_t)(wa >> 16);
+        if (e & 0x00800000u) *p++ = (uint16_t)wb;
+        if (e & 0x80000000u) *p++ = (uint16_t)(wb >> 16);
+    }
+}
+
+// ===========================================================================
+// UTF-16LE -> UTF-8 chunk (paper Sec. 7)
+//
+// Output length per word (Sec. 7, plan of attack): 1 byte below U+0080, 2
+// below U+0800, 3 for other BMP words, 4 for a high surrogate (the pair), 0
+// for a low surrogate; counted two words at a time on 16-bit lanes.
+//
+// Paths: like the paper's fast paths (Sec. 7.1), each warp picks one from its
+// own words: all below U+0800 (1-2 byte encoder), no surrogates (1-3 byte
+// encoder) - neither needs validation - or the general path with the
+// surrogate join and the sequencing check of Sec. 7.4: a high surrogate not
+// followed by a low one is LONE_HIGH at the high, a low surrogate not
+// preceded by a high one is LONE_LOW at the low.
+//
+// Encoding (Fig. 1(a), Sec. 7.2-7.3): pairs are joined with
+// (hi << 10) + lo + 0xFCA02400 (32-bit wrap); the 6-bit groups of the code
+// point get the tag bits C0/E0/F0 (lead) and 80 (continuation).
+// ===========================================================================
+
+__device__ __forceinline__ uint32_t ge80_lanes(uint32_t w)    // word >= 0x0080, bit 15 per lane
+{
+    return (((w & 0x7F807F80u) + 0x7F807F80u) | w) & 0x80008000u;
+}
+__device__ __forceinline__ uint32_t ge800_lanes(uint32_t w)   // word >= 0x0800
+{
+    return (((w & 0x78007800u) + 0x78007800u) | w) & 0x80008000u;
+}
+__device__ __forceinline__ uint32_t surr_lanes(uint32_t w)    // D800-DFFF (exact: low 11 bits zero)
+{
+    const uint32_t v = (w & 0xF800F800u) ^ 0xD800D800u;
+    return (v - 0x00010001u) & ~v & 0x80008000u;
+}
+
+__device__ __forceinline__ uint32_t lane16(const uint32_t *w, int i)   // word i, i in [-2, 18)
+{
+    return (w[(i + 2) >> 1] >> (16 * ((i + 2) & 1))) & 0xFFFFu;
+}
+
+// 1-2 byte encoder (Sec. 7.1): 110LKJHG 10FEDCBA from 00000LKJHGFEDCBA.
+__device__ __forceinline__ uint32_t enc2(uint32_t u)
+{
+    return (((u << 8) | (u >> 6)) & 0x3F3Fu) | 0x80C0u;
+}
+
+// 3-byte encoder: 1110RQPN 10MLKJHG 10FEDCBA.
+__device__ __forceinline__ uint32_t enc3(uint32_t u)
+{
+    return (u >> 12) | ((u << 2) & 0x3F00u) | ((u << 16) & 0x3F0000u) | 0x8080E0u;
+}
+
+struct St16 {
+    uint32_t w[10];    // w[0]: words -2,-1; w[1..8]: own words 0..15; w[9]: words 16,17
+    uint32_t vmask;
+    bool edge, general, only12;
+};
+
+__device__ __forceinline__ uint32_t unit_keep(int64_t u, int64_t lo, int64_t hi)
+{
+    return (u >= lo && u < hi) ? 0xFFFFu : 0u;
+}
+
+__device__ __forceinline__ uint32_t chunk16_phase1(St16 &st, const uint8_t *stage, int64_t vt,
+                                                   int64_t lo, int64_t hi)
+{
+    const uint8_t *sp = stage + kHalo + 32 * threadIdx.x;
+    const uint4 a = *reinterpret_cast<const uint4 *>(sp);
+    const uint4 b = *reinterpret_cast<const uint4 *>(sp + 16);
+    uint32_t *w = st.w;
+    w[1] = a.x; w[2] = a.y; w[3] = a.z; w[4] = a.w;
+    w[5] = b.x; w[6] = b.y; w[7] = b.z; w[8] = b.w;
+    w[0] = *reinterpret_cast<const uint32_t *>(sp - 4);
+    w[9] = *reinterpret_cast<const uint32_t *>(sp + 32);
+    st.vmask = 0xFFFFu;
+    st.edge = vt < lo || vt + 16 > hi;
+    if (st.edge) {
+        st.vmask = 0;
+#pragma unroll
+        for (int i = 0; i < 16; i++)
+            if (vt + i >= lo && vt + i < hi) st.vmask |= 1u << i;
+#pragma unroll
+        for (int j = 0; j < 8; j++)
+            w[1 + j] &= unit_keep(vt + 2 * j, lo, hi) | (unit_keep(vt + 2 * j + 1, lo, hi) << 16);
+    }
+    if (vt - 2 < lo || vt + 18 > hi) {
+        w[0] &= unit_keep(vt - 2, lo, hi) | (unit_keep(vt - 1, lo, hi) << 16);
+        w[9] &= unit_keep(vt + 16, lo, hi) | (unit_keep(vt + 17, lo, hi) << 16);
+    }
+    uint32_t cnt = 0, any800 = 0, anysur = 0;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        const uint32_t x = w[1 + j];
+        const uint32_t ga = ge80_lanes(x), gb = ge800_lanes(x), s = surr_lanes(x);
+        const uint32_t lo_bit = (x << 5) & 0x80008000u;   // bit 10: low surrogate
+        uint32_t vm = 0x80008000u;
+        if (st.edge)
+            vm = (((st.vmask >> (2 * j)) & 1u) << 15) | (((st.vmask >> (2 * j + 1)) & 1u) << 31);
+        // 1 + [>=80] + [>=800] + [high] - 3 [low]
+        cnt += __popc(vm) + __popc(ga & vm) + __popc(gb & vm) + __popc(s & ~lo_bit & vm) -
+               3u * __popc(s & lo_bit & vm);
+        any800 |= gb;
+        anysur |= s;
+    }
+    st.general = __any_sync(kFull, anysur != 0 || st.edge);
+    st.only12 = !__any_sync(kFull, any800 != 0);
+    return cnt;
+}
+
+template <bool kWrite>
+__device__ __forceinline__ void chunk16_phase2(const St16 &st, uint8_t *obuf, uint32_t t_off,
+                                               int64_t vt, int64_t lo, unsigned long long *s_err)
+{
+    const uint32_t *w = st.w;
+    if (!st.general) {
+        // no surrogates in this warp: every word is valid
+        if (!kWrite) return;
+        uint8_t *p = obuf + t_off;
+        if (st.only12) {
+#pragma unroll
+            for (int i = 0; i < 16; i++) {
+                const uint32_t u = lane16(w, i);
+                const bool big = u >= 0x80u;
+                const uint32_t v = big ? enc2(u) : u;
+                p[0] = (uint8_t)v;
+                if (big) p[1] = (uint8_t)(v >> 8);
+                p += big ? 2 : 1;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 16; i++) {
+                const uint32_t u = lane16(w, i);
+                const bool c2 = u >= 0x80u, c3 = u >= 0x800u;
+                const uint32_t v = c3 ? enc3(u) : (c2 ? enc2(u) : u);
+                p[0] = (uint8_t)v;
+                if (c2) p[1] = (uint8_t)(v >> 8);
+                if (c3) p[2] = (uint8_t)(v >> 16);
+                p += 1 + (c2 ? 1 : 0) + (c3 ? 1 : 0);
+            }
+        }
+        return;
+    }
+    uint64_t key = ~0ull;
+    uint32_t o = t_off;
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+        const uint32_t u = lane16(w, i), pv = lane16(w, i - 1), nx = lane16(w, i + 1);
+        const bool is_hi = (u & 0xFC00u) == 0xD800u;
+        const bool is_lo = (u & 0xFC00u) == 0xDC00u;
+        uint32_t kind = 0;
+        if (is_hi && (nx & 0xFC00u) != 0xDC00u) kind = kLoneHigh;
+        if (is_lo && (pv & 0xFC00u) != 0xD800u) kind = kLoneLow;
+        const bool c2 = u >= 0x80u, c3 = u >= 0x800u;
+        const uint32_t len = is_lo ? 0u : (is_hi ? 4u : 1u + (c2 ? 1u : 0u) + (c3 ? 1u : 0u));
+        uint32_t v;
+        if (is_hi) {
+            const uint32_t cp = (u << 10) + nx + 0xFCA02400u;
+            v = (cp >> 18) | ((cp >> 4) & 0x3F00u) | ((cp << 10) & 0x3F0000u) |
+                ((cp << 24) & 0x3F000000u) | 0x808080F0u;
+        } else {
+            v = c3 ? enc3(u) : (c2 ? enc2(u) : u);
+        }
+        if ((st.vmask >> i) & 1u) {
+            if (kWrite && o + len <= kStage16Bytes) {
+                uint8_t *q = obuf + o;
+                if (len >= 1) q[0] = (uint8_t)v;
+                if (len >= 2) q[1] = (uint8_t)(v >> 8);
+                if (len >= 3) q[2] = (uint8_t)(v >> 16);
+                if (len >= 4) q[3] = (uint8_t)(v >> 24);
+            }
+            if (kind != 0 && key == ~0ull) key = err_key((uint64_t)(vt + i - lo), kind, o);
+            o += len;
+        }
+    }
+    if (key != ~0ull) atomicMin(s_err, key);
+}
+
+// ===========================================================================
+// The persistent kernel
+// ===========================================================================
+
+struct Ring {
+    uint64_t full[kStages];        // mbarrier per stage (TMA completion)
+    Item item[kStages];
+    uint32_t chunk[kStages], itidx[kStages], end[kStages];
+};
+
+// Thread 0: claim the next chunk and start its TMA load into `slot`.
+// Returns false (and marks the slot as the end) when the job is exhausted.
+__device__ __forceinline__ bool produce(const Job &J, int slot, uint8_t *stages, Ring &R)
+{
+    const uint32_t c = atomicAdd(J.claim, 1u);
+    if (c >= J.total_chunks) {
+        R.end[slot] = 1;
+        mbar_arrive(&R.full[slot]);
+        return false;
+    }
+    const uint32_t it = J.chunk_item ? J.chunk_item[c] : 0u;
+    const Item I = J.items ? J.items[it] : J.item0;
+    R.item[slot] = I;
+    R.chunk[slot] = c;
+    R.itidx[slot] = it;
+    R.end[slot] = 0;
+    const int64_t ub = (I.op & kOpUtf16) ? 2 : 1;
+    const int64_t v0b = (int64_t)(c - I.chunk_base) * kChunkBytes;   // virtual byte offset
+    const int64_t endb = (((int64_t)I.head + (int64_t)I.n) * ub + 15) & ~(int64_t)15;
+    int64_t lo_b = v0b - (int64_t)kHalo;
+    if (lo_b < 0) lo_b = 0;
+    int64_t hi_b = v0b + (int64_t)(kChunkBytes + kHalo);
+    if (hi_b > endb) hi_b = endb;
+    uint8_t *dst = stages + (size_t)slot * kStageBytes + (lo_b - (v0b - (int64_t)kHalo));
+    fence_proxy_async_smem();
+    if (hi_b > lo_b) {
+        mbar_arrive_expect_tx(&R.full[slot], (uint32_t)(hi_b - lo_b));
+        tma_load_1d(dst, I.in_al + lo_b, (uint32_t)(hi_b - lo_b), &R.full[slot]);
+    } else {
+        mbar_arrive(&R.full[slot]);
+    }
+    return true;
+}
+
+struct Pending {                 // a processed chunk waiting for its offset
+    Item item;
+    uint32_t chunk, itidx, agg, end;
+};
+
+// One warp copies nbytes from shared memory (4-byte aligned, readable 16
+// bytes past the end) to global dst: 16-byte aligned vector stores for the
+// body, byte stores at the two unaligned edges.
+__device__ __forceinline__ void warp_store_bytes(const uint8_t *s_src, uint8_t *dst,
+                                                 uint32_t nbytes)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const uintptr_t d = reinterpret_cast<uintptr_t>(dst);
+    uint32_t head = (uint32_t)((16u - (d & 15u)) & 15u);
+    if (head > nbytes) head = nbytes;
+    if (lane < head) dst[lane] = s_src[lane];
+    const uint32_t nblk = (nbytes - head) >> 4;
+    const uint32_t *sw = reinterpret_cast<const uint32_t *>(s_src);
+    for (uint32_t b = lane; b < nblk; b += 32) {
+        const uint32_t so = head + 16u * b;
+        const uint32_t *q = sw + (so >> 2);
+        const uint32_t sh = (so & 3u) * 8u;
+        const uint32_t w0 = q[0], w1 = q[1], w2 = q[2], w3 = q[3], w4 = q[4];
+        uint4 v;
+        v.x = __funnelshift_r(w0, w1, sh);
+        v.y = __funnelshift_r(w1, w2, sh);
+        v.z = __funnelshift_r(w2, w3, sh);
+        v.w = __funnelshift_r(w3, w4, sh);
+        *reinterpret_cast<uint4 *>(dst + so) = v;
+    }
+    const uint32_t tail0 = head + 16u * nblk;
+    if (lane < nbytes - tail0) dst[tail0 + lane] = s_src[tail0 + lane];
+}
+
+// Warps 0-7 (compute): per chunk, wait for its stage, classify and count it,
+// scan, publish the aggregate, hand the chunk to the store warp (pend_bar),
+// assemble its output into a staging buffer and signal it (staged_bar). They
+// never wait on a look-back: only on input (full) and on a free staging
+// buffer (free_bar).
+// Warp 8 (look-back and store): per handed-over chunk, look back, publish the
+// inclusive prefix, wait for the staged output, write it at its offset,
+// publish errors, finish the item when it was its last chunk, and free the
+// staging buffer.
+template <bool kWrite>
+__global__ void __launch_bounds__(kBlock, kMinBlocks)
+transcode_kernel(const Job J)
+{
+    extern __shared__ __align__(128) uint8_t dyn_smem[];
+    uint8_t *const stages = dyn_smem;
+    uint8_t *const obufs = dyn_smem + kStages * kStageBytes;
+    __shared__ __align__(8) Ring R;
+    __shared__ __align__(8) uint64_t pend_bar[2], staged_bar[2], free_bar[2];
+    __shared__ Pending s_pend[2];
+    __shared__ unsigned long long s_err[2];
+    __shared__ uint32_t s_warp[kThreads / 32 + 1];
+    __shared__ uint32_t s_epoch;
+
+    const uint32_t tid = threadIdx.x;
+    if (tid == 0) {
+        for (int s = 0; s < kStages; s++) mbar_init(&R.full[s], 1);
+        for (int s = 0; s < 2; s++) {
+            mbar_init(&pend_bar[s], 1);
+            mbar_init(&staged_bar[s], kThreads);
+            mbar_init(&free_bar[s], 1);
+            s_err[s] = ~0ull;
+        }
+        fence_mbar_init();
+        s_epoch = *reinterpret_cast<volatile unsigned int *>(J.epoch);
+    }
+    __syncthreads();
+    const uint32_t epoch = s_epoch;
+
+    if (tid >= kThreads) {
+        // ---- look-back and store warp -----------------------------------------
+        const bool lead = tid == kThreads;
+        bool failed = false;
+        for (uint32_t j = 0;; j++) {
+            const int p = j & 1;
+            const uint32_t par = (j >> 1) & 1u;
+            if (!mbar_wait(&pend_bar[p], par)) {
+                failed = true;
+                break;
+            }
+            const Pending &P = s_pend[p];
+            if (P.end) break;
+            const uint32_t k = P.chunk - P.item.chunk_base;
+            uint64_t excl = 0;
+            if (k > 0) {
+                excl = lookback(J.status + P.item.chunk_base, k, epoch, J.flags);
+                if (lead)
+                    st_relaxed(&J.status[P.chunk], pack_status(kFlagInclusive, epoch, excl + P.agg));
+            }
+            if (!mbar_wait(&staged_bar[p], par)) {
+                failed = true;
+                break;
+            }
+            if (kWrite) {
+                const bool u16 = (P.item.op & kOpUtf16) != 0;
+                const uint32_t ub = u16 ? 1u : 2u;                       // output unit bytes
+                const uint32_t stage_units = u16 ? kStage16Bytes : kStage8Units;
+                if (excl < P.item.cap) {
+                    const uint64_t room = P.item.cap - excl;
+                    uint32_t nw = P.agg < stage_units ? P.agg : stage_units;
+                    if (nw > room) nw = (uint32_t)room;
+                    warp_store_bytes(obufs + (size_t)p * kOutBufBytes, P.item.out + excl * ub, nw * ub);
+                }
+            }
+            if (lead) {
+                const uint64_t key = s_err[p];
+                if (key != ~0ull) {
+                    J.err_prefix[P.chunk] = excl + (key & 0x7FFFu);
+                    atomicMin(&J.item_err[P.itidx], ((key >> 23) << 8) | ((key >> 15) & 0xFFu));
+                    s_err[p] = ~0ull;
+                }
+                __threadfence();
+                if (atomicAdd(&J.item_done[P.itidx], 1u) == P.item.nchunks - 1)
+                    finalize_item(J, P.itidx, P.item);
+            }
+            __syncwarp();
+            if (lead) mbar_arrive(&free_bar[p]);
+        }
+        // last CTA out: check that every chunk id was handed out exactly once,
+        // advance the epoch, and reset the job's counters for the next launch
+        if (lead) {
+            if (failed) atomicOr(J.flags, 1u);
+            __threadfence();
+            if (atomicAdd(J.exit_count, 1u) == gridDim.x - 1) {
+                const unsigned int claims = atomicExch(J.claim, 0u);
+                if (claims != J.total_chunks + gridDim.x) {
+                    // counters were left dirty by an aborted launch: no item
+                    // was finished reliably
+                    for (uint32_t it = 0; it < J.num_items; it++) {
+                        const Item &X = J.items ? J.items[it] : J.item0;
+                        volatile ResultSlot *r = X.result;
+                        r->status = kDeviceError;
+                        r->reserved = 0;
+                        r->in_offset = 0;
+                        r->out_len = 0;
+                    }
+                }
+                const uint32_t next = (epoch + 1) & kEpochMask;
+                if (next == 0)   // wrap: stale words of epoch 0 must not look ready
+                    for (uint32_t i = 0; i < J.status_capacity; i++) J.status[i] = 0;
+                *J.epoch = next;
+                *J.exit_count = 0;
+                *J.flags = 0;
+                __threadfence_system();
+            }
+        }
+        return;
+    }
+
+    // ---- compute warps ------------------------------------------------------
+    bool producing = true;   // meaningful in thread 0 only
+    if (tid == 0)
+        for (int s = 0; s < kStages - 1 && producing; s++) producing = produce(J, s, stages, R);
+
+    uint32_t iter = 0;
+    bool failed = false;
+    while (true) {
+        const int slot = iter % kStages;
+        const int p = iter & 1;
+        if (tid == 0 && producing) producing = produce(J, (iter + kStages - 1) % kStages, stages, R);
+        const bool ok = mbar_wait(&R.full[slot], (iter / kStages) & 1u);
+        if (cw_sync_or(!ok)) {
+            failed = true;
+            break;
+        }
+        if (R.end[slot]) break;
+        const Item I = R.item[slot];
+        const uint32_t c = R.chunk[slot];
+        const uint32_t it = R.itidx[slot];
+        const uint8_t *stage = stages + (size_t)slot * kStageBytes;
+        uint8_t *obuf = obufs + (size_t)p * kOutBufBytes;
+        const int64_t lo = I.head, hi = (int64_t)I.head + (int64_t)I.n;
+        const uint32_t k = c - I.chunk_base;
+        uint32_t agg, t_off;
+        // publish the aggregate, wait until the store warp is done with this
+        // staging buffer (chunk iter-2), then hand the chunk over
+        auto hand_over = [&]() -> bool {
+            if (tid == 0)
+                st_relaxed(&J.status[c], pack_status(k == 0 ? kFlagInclusive : kFlagAggregate, epoch, agg));
+            if (iter >= 2 && !mbar_wait(&free_bar[p], ((iter - 2) >> 1) & 1u)) return false;
+            if (tid == 0) {
+                Pending &P = s_pend[p];
+                P.item = I;
+                P.chunk = c;
+                P.itidx = it;
+                P.agg = agg;
+                P.end = 0;
+                mbar_arrive(&pend_bar[p]);
+            }
+            return true;
+        };
+        bool ok2;
+        if (I.op & kOpUtf16) {
+            const int64_t vt = (int64_t)k * kChunk16 + 16 * tid;
+            St16 st;
+            const uint32_t cnt = chunk16_phase1(st, stage, vt, lo, hi);
+            t_off = block_exclusive_scan(cnt, s_warp, &agg);
+            ok2 = hand_over();
+            if (ok2) chunk16_phase2<kWrite>(st, obuf, t_off, vt, lo, &s_err[p]);
+        } else {
+            const int64_t vt = (int64_t)k * kChunk8 + 32 * tid;
+            St8 st;
+            const uint32_t cnt = chunk8_phase1(st, stage, vt, lo, hi);
+            t_off = block_exclusive_scan(cnt, s_warp, &agg);
+            ok2 = hand_over();
+            if (ok2) chunk8_phase2<kWrite>(st, obuf, t_off, vt, lo, &s_err[p]);
+        }
+        mbar_arrive(&staged_bar[p]);
+        if (cw_sync_or(!ok2)) {
+            failed = true;
+            break;
+        }
+        iter++;
+    }
+    // stop the store warp once it is done with chunk iter-2's buffer
+    if (tid == 0) {
+        if (failed) atomicOr(J.flags, 1u);
+        if (iter >= 2) mbar_wait(&free_bar[iter & 1], ((iter - 2) >> 1) & 1u);
+        Pending &P = s_pend[iter & 1];
+        P.end = 1;
+        mbar_arrive(&pend_bar[iter & 1]);
+    }
+}
+
+int g_max_grid[64] = {0};
+
+}  // namespace
+
+size_t job_smem_bytes(bool write)
+{
+    return (size_t)kStages * kStageBytes + (write ? 2 * (size_t)kOutBufBytes : 0);
+}
+
+int job_max_grid(int device)
+{
+    if (device < 0 || device >= 64) return 0;
+    if (g_max_grid[device]) return g_max_grid[device];
+    int sms = 0, per = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+        return 0;
+    for (int w = 0; w < 2; w++) {
+        const void *fn = w ? (const void *)transcode_kernel<true> : (const void *)transcode_kernel<false>;
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)job_smem_bytes(w != 0)) != cudaSuccess)
+            return 0;
+    }
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, transcode_kernel<true>, kBlock,
+                                                      job_smem_bytes(true)) != cudaSuccess ||
+        per < 1)
+        per = 1;
+    g_max_grid[device] = sms * per;
+    return g_max_grid[device];
+}
+
+cudaError_t launch_job(const Job &J, bool write, int grid, cudaStream_t stream)
+{
+    if (write)
+        transcode_kernel<true><<<grid, kBlock, job_smem_bytes(true), stream>>>(J);
+    else
+        transcode_kernel<false><<<grid, kBlock, job_smem_bytes(false), stream>>>(J);
+    return cudaGetLastError();
+}
+
+__global__ void write_result_kernel(ResultSlot *dst, int32_t status, uint64_t in_offset,
+                                    uint64_t out_len)
+{
+    volatile ResultSlot *r = dst;
+    r->status = status;
+    r->reserved = 0;
+    r->in_offset = in_offset;
+    r->out_len = out_len;
+    __threadfence_system();
+}
+
+cudaError_t launch_write_result(ResultSlot *dst, int32_t status, uint64_t in_offset,
+                                uint64_t out_len, cudaStream_t stream)
+{
+    write_result_kernel<<<1, 1, 0, stream>>>(dst, status, in_offset, out_len);
+    return cudaGetLastError();
+}
+
+Item make_item(const void *in, uint64_t n, bool utf16, void *out, uint64_t cap, bool write,
+               ResultSlot *result, uint32_t chunk_base)
+{
+    Item I{};
+    const uintptr_t p = reinterpret_cast<uintptr_t>(in);
+    if (n == 0) {
+        I.in_al = nullptr;
+        I.head = 0;
+    } else {
+        I.in_al = reinterpret_cast<const uint8_t *>(p & ~(uintptr_t)15u);
+        I.head = (uint32_t)(utf16 ? (p & 15u) >> 1 : (p & 15u));
+    }
+    I.n = n;
+    I.out = static_cast<uint8_t *>(out);
+    I.cap = write ? cap : 0;
+    I.result = result;
+    I.op = (utf16 ? kOpUtf16 : 0u) | (write ? kOpWrite : 0u);
+    I.chunk_base = chunk_base;
+    const uint64_t units = utf16 ? kChunk16 : kChunk8;
+    const uint64_t nch = n ? (I.head + n + units - 1) / units : 1;
+    I.nchunks = (uint32_t)nch;
+    return I;
+}
+
+}  // namespace gbu

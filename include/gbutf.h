@@ -138,6 +138,50 @@ gbu_result gbu_utf8_to_utf16le_host(gbu_ctx *ctx, const uint8_t *h_in, uint64_t 
 gbu_result gbu_utf16le_to_utf8_host(gbu_ctx *ctx, const uint16_t *h_in, uint64_t n_units,
                                     uint8_t *h_out, uint64_t cap_bytes, void *stream);
 
+/* ---- Batches: many independent inputs in one persistent launch -------------
+ *
+ * The paper transcodes one buffer per call; a batch runs many such calls (any
+ * mix of directions and of transcoding / length-only) in ONE launch of the
+ * persistent kernel: the chunks of all inputs are numbered consecutively and
+ * handed out in order, every input keeps its own prefix scan, first error and
+ * result, so each result equals that of the single-buffer call on the same
+ * input. */
+typedef enum gbu_op {
+    GBU_OP_UTF8_TO_UTF16LE = 0,           /* as gbu_utf8_to_utf16le            */
+    GBU_OP_UTF16LE_TO_UTF8 = 1,           /* as gbu_utf16le_to_utf8            */
+    GBU_OP_UTF16_LENGTH_FROM_UTF8 = 2,    /* as gbu_utf16_length_from_utf8     */
+    GBU_OP_UTF8_LENGTH_FROM_UTF16LE = 3   /* as gbu_utf8_length_from_utf16le   */
+} gbu_op;
+
+typedef struct gbu_batch_item {
+    const void *in;      /* device pointer: UTF-8 bytes or UTF-16LE words (2-byte aligned) */
+    uint64_t n;          /* input units                                                  */
+    void *out;           /* device pointer, or NULL for the length-only ops              */
+    uint64_t cap;        /* output capacity in units (ignored for length-only ops)       */
+    int32_t op;          /* gbu_op                                                        */
+    uint32_t reserved;   /* zero                                                          */
+} gbu_batch_item;
+
+/* Plan a batch on the context: validate the `count` host-side items, lay out
+ * their chunks and upload the plan to device memory owned by the context
+ * (allocated or grown here; returns after the upload). Results of the batch
+ * go to `results[i]` (device memory, or pinned host memory mapped into the
+ * device's address space), one gbu_result per item, with the semantics of the
+ * corresponding single-buffer call. A plan stays valid until the next plan on
+ * the context and may be launched any number of times. Returns GBU_OK,
+ * GBU_INVALID_ARG (bad item: index not reported) or GBU_DEVICE_ERROR. */
+int32_t gbu_batch_plan(gbu_ctx *ctx, const gbu_batch_item *items, uint32_t count,
+                       gbu_result *results, void *stream);
+
+/* Enqueue one launch of the planned batch on `stream` (no host work, no
+ * allocation; it may be captured into a CUDA graph by the caller). Results are
+ * stored when the stream reaches the end of the work. */
+int32_t gbu_batch_launch(gbu_ctx *ctx, void *stream);
+
+/* Same, through a CUDA graph the context captures once per plan and replays
+ * on `stream` (lowest launch overhead for repeated batches). */
+int32_t gbu_batch_launch_graph(gbu_ctx *ctx, void *stream);
+
 /* No-allocation form of gbu_utf8_to_utf16le. The paper has no counterpart to
  * this call: it is for callers that may not allocate device memory (another
  * component owns the device's memory, or an allocation's implicit device

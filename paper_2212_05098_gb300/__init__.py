@@ -52,6 +52,17 @@ class Result:
         return status_name(self.status)
 
 
+GBU_OP_UTF8_TO_UTF16LE = 0
+GBU_OP_UTF16LE_TO_UTF8 = 1
+GBU_OP_UTF16_LENGTH_FROM_UTF8 = 2
+GBU_OP_UTF8_LENGTH_FROM_UTF16LE = 3
+
+
+class gbu_batch_item(ctypes.Structure):
+    _fields_ = [("in_", ctypes.c_void_p), ("n", ctypes.c_uint64), ("out", ctypes.c_void_p),
+                ("cap", ctypes.c_uint64), ("op", ctypes.c_int32), ("reserved", ctypes.c_uint32)]
+
+
 # name -> (restype, argtypes)
 _VP, _U64, _I32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int32
 _RP = ctypes.POINTER(gbu_result)
@@ -69,6 +80,9 @@ SIGNATURES = {
     "gbu_utf8_length_from_utf16le_async": (_I32, [_VP, _VP, _U64, _VP, _VP]),
     "gbu_utf8_to_utf16le_host": (gbu_result, [_VP, _VP, _U64, _VP, _U64, _VP]),
     "gbu_utf16le_to_utf8_host": (gbu_result, [_VP, _VP, _U64, _VP, _U64, _VP]),
+    "gbu_batch_plan": (_I32, [_VP, ctypes.POINTER(gbu_batch_item), ctypes.c_uint32, _VP, _VP]),
+    "gbu_batch_launch": (_I32, [_VP, _VP]),
+    "gbu_batch_launch_graph": (_I32, [_VP, _VP]),
     "gbu_utf8_to_utf16le_noalloc": (gbu_result, [_VP, _U64, _VP, _U64, _VP]),
     "gbu_status_name": (ctypes.c_char_p, [_I32]),
     "gbu_kernel_launch_count": (_U64, []),
@@ -156,6 +170,22 @@ def gbu_utf8_to_utf16le_host(ctx, h_in, n_bytes, h_out, cap_units, stream=0) -> 
 
 def gbu_utf16le_to_utf8_host(ctx, h_in, n_units, h_out, cap_bytes, stream=0) -> Result:
     return _res(load().gbu_utf16le_to_utf8_host(ctx, h_in, n_units, h_out, cap_bytes, stream))
+
+
+def gbu_batch_plan(ctx, items, results_ptr, stream=0) -> int:
+    """items: sequence of (in_ptr, n, out_ptr, cap, op) tuples or gbu_batch_item."""
+    arr = (gbu_batch_item * max(1, len(items)))()
+    for i, it in enumerate(items):
+        arr[i] = it if isinstance(it, gbu_batch_item) else gbu_batch_item(*it, 0)
+    return load().gbu_batch_plan(ctx, arr, len(items), results_ptr, stream)
+
+
+def gbu_batch_launch(ctx, stream=0) -> int:
+    return load().gbu_batch_launch(ctx, stream)
+
+
+def gbu_batch_launch_graph(ctx, stream=0) -> int:
+    return load().gbu_batch_launch_graph(ctx, stream)
 
 
 def gbu_utf8_to_utf16le_noalloc(d_in, n_bytes, d_out, cap_units, stream=0) -> Result:

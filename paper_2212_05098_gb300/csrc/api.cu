@@ -45,6 +45,16 @@ struct gbu_ctx {
     gbu_result *d_result = nullptr;   // device alias of h_result
     uint8_t *io = nullptr;            // device staging for the host-buffer forms
     size_t io_bytes = 0;
+    // planned batch
+    gbu::Item *d_items = nullptr, *h_items = nullptr;            // device / pinned host
+    uint32_t *d_chunk_item = nullptr, *h_chunk_item = nullptr;
+    unsigned long long *d_item_err = nullptr;
+    unsigned int *d_item_done = nullptr;
+    uint64_t items_cap = 0, chunk_map_cap = 0;
+    uint32_t batch_items = 0, batch_chunks = 0;
+    bool batch_write = false;
+    cudaStream_t capture_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
 };
 
 namespace {
@@ -187,6 +197,14 @@ void gbu_destroy(gbu_ctx *c)
     if (!c) return;
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+    if (c->d_items) cudaFree(c->d_items);
+    if (c->h_items) cudaFreeHost(c->h_items);
+    if (c->d_chunk_item) cudaFree(c->d_chunk_item);
+    if (c->h_chunk_item) cudaFreeHost(c->h_chunk_item);
+    if (c->d_item_err) cudaFree(c->d_item_err);
+    if (c->d_item_done) cudaFree(c->d_item_done);
     if (c->scratch) cudaFree(c->scratch);
     if (c->io) cudaFree(c->io);
     if (c->h_result) cudaFreeHost(c->h_result);
@@ -298,6 +316,160 @@ gbu_result gbu_utf16le_to_utf8_host(gbu_ctx *c, const uint16_t *h_in, uint64_t n
                                     uint64_t cap, void *stream)
 {
     return run_host(c, Op::U16toU8, h_in, n, h_out, cap, stream);
+}
+
+// ---- batches -----------------------------------------------------------------
+
+static bool grow_batch(gbu_ctx *c, uint64_t items, uint64_t chunks)
+{
+    if (items > c->items_cap) {
+        uint64_t want = c->items_cap ? c->items_cap : 64;
+        while (want < items) want *= 2;
+        if (c->d_items) cudaFree(c->d_items);
+        if (c->h_items) cudaFreeHost(c->h_items);
+        if (c->d_item_err) cudaFree(c->d_item_err);
+        if (c->d_item_done) cudaFree(c->d_item_done);
+        c->d_items = nullptr; c->h_items = nullptr; c->d_item_err = nullptr; c->d_item_done = nullptr;
+        c->items_cap = 0;
+        if (!ok(cudaMalloc(&c->d_items, want * sizeof(Item))) ||
+            !ok(cudaHostAlloc(&c->h_items, want * sizeof(Item), cudaHostAllocDefault)) ||
+            !ok(cudaMalloc(&c->d_item_err, want * 8)) || !ok(cudaMalloc(&c->d_item_done, want * 4)))
+            return false;
+        c->items_cap = want;
+    }
+    if (chunks > c->chunk_map_cap) {
+        uint64_t want = c->chunk_map_cap ? c->chunk_map_cap : 1024;
+        while (want < chunks) want *= 2;
+        if (c->d_chunk_item) cudaFree(c->d_chunk_item);
+        if (c->h_chunk_item) cudaFreeHost(c->h_chunk_item);
+        c->d_chunk_item = nullptr; c->h_chunk_item = nullptr;
+        c->chunk_map_cap = 0;
+        if (!ok(cudaMalloc(&c->d_chunk_item, want * 4)) ||
+            !ok(cudaHostAlloc(&c->h_chunk_item, want * 4, cudaHostAllocDefault)))
+            return false;
+        c->chunk_map_cap = want;
+    }
+    return true;
+}
+
+int32_t gbu_batch_plan(gbu_ctx *c, const gbu_batch_item *items, uint32_t count,
+                       gbu_result *results, void *stream)
+{
+    if (!c || (count && (!items || !results))) return GBU_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!ok(cudaSetDevice(c->device))) return GBU_DEVICE_ERROR;
+    // validate and count chunks
+    uint64_t chunks = 0;
+    bool any_write = false;
+    for (uint32_t i = 0; i < count; i++) {
+        const gbu_batch_item &b = items[i];
+        if (b.op < GBU_OP_UTF8_TO_UTF16LE || b.op > GBU_OP_UTF8_LENGTH_FROM_UTF16LE)
+            return GBU_INVALID_ARG;
+        const bool utf16 = b.op == GBU_OP_UTF16LE_TO_UTF8 || b.op == GBU_OP_UTF8_LENGTH_FROM_UTF16LE;
+        const bool write = b.op <= GBU_OP_UTF16LE_TO_UTF8;
+        if (b.n >= kMaxUnits || (b.n && !b.in)) return GBU_INVALID_ARG;
+        if (utf16 && (reinterpret_cast<uintptr_t>(b.in) & 1u)) return GBU_INVALID_ARG;
+        if (write && b.cap && !b.out) return GBU_INVALID_ARG;
+        if (write && !utf16 && (reinterpret_cast<uintptr_t>(b.out) & 1u)) return GBU_INVALID_ARG;
+        any_write |= write;
+        const uint64_t units = utf16 ? kChunk16 : kChunk8;
+        const uint64_t head = b.n ? (utf16 ? ((reinterpret_cast<uintptr_t>(b.in) & 15u) >> 1)
+                                           : (reinterpret_cast<uintptr_t>(b.in) & 15u))
+                                  : 0;
+        chunks += b.n ? (head + b.n + units - 1) / units : 1;
+    }
+    if (chunks >= (1ull << 32)) return GBU_INVALID_ARG;
+    if (!ok(cudaStreamSynchronize(s))) return GBU_DEVICE_ERROR;   // host staging is reused
+    if (!grow_batch(c, count ? count : 1, chunks ? chunks : 1)) return GBU_DEVICE_ERROR;
+    uint32_t base = 0;
+    for (uint32_t i = 0; i < count; i++) {
+        const gbu_batch_item &b = items[i];
+        const bool utf16 = b.op == GBU_OP_UTF16LE_TO_UTF8 || b.op == GBU_OP_UTF8_LENGTH_FROM_UTF16LE;
+        const bool write = b.op <= GBU_OP_UTF16LE_TO_UTF8;
+        Item I = make_item(b.in, b.n, utf16, b.out, b.cap, write,
+                           reinterpret_cast<ResultSlot *>(results + i), base);
+        c->h_items[i] = I;
+        for (uint32_t k = 0; k < I.nchunks; k++) c->h_chunk_item[base + k] = i;
+        base += I.nchunks;
+    }
+    int32_t st = ensure_scratch(c, chunks ? chunks : 1, s);
+    if (st != GBU_OK) return st;
+    if (count) {
+        if (!ok(cudaMemcpyAsync(c->d_items, c->h_items, count * sizeof(Item), cudaMemcpyHostToDevice, s)) ||
+            !ok(cudaMemcpyAsync(c->d_chunk_item, c->h_chunk_item, chunks * 4, cudaMemcpyHostToDevice, s)) ||
+            !ok(cudaMemsetAsync(c->d_item_err, 0xFF, (size_t)count * 8, s)) ||
+            !ok(cudaMemsetAsync(c->d_item_done, 0, (size_t)count * 4, s)) ||
+            !ok(cudaStreamSynchronize(s)))
+            return GBU_DEVICE_ERROR;
+    }
+    c->batch_items = count;
+    c->batch_chunks = (uint32_t)chunks;
+    c->batch_write = any_write;
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    return GBU_OK;
+}
+
+static int32_t batch_enqueue(gbu_ctx *c, cudaStream_t s)
+{
+    if (c->batch_items == 0) return GBU_OK;
+    Job J{};
+    J.items = c->d_items;
+    J.chunk_item = c->d_chunk_item;
+    J.num_items = c->batch_items;
+    J.total_chunks = c->batch_chunks;
+    attach_scratch(c, J);
+    J.item_err = c->d_item_err;
+    J.item_done = c->d_item_done;
+    int grid = job_max_grid(c->device);
+    if (grid <= 0) return GBU_DEVICE_ERROR;
+    if ((uint32_t)grid > J.total_chunks) grid = (int)J.total_chunks;
+    const cudaError_t e = launch_job(J, c->batch_write, grid, s);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return ok(e) ? GBU_OK : GBU_DEVICE_ERROR;
+}
+
+int32_t gbu_batch_launch(gbu_ctx *c, void *stream)
+{
+    if (!c) return GBU_INVALID_ARG;
+    if (!ok(cudaSetDevice(c->device))) return GBU_DEVICE_ERROR;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (c->dirty && ensure_scratch(c, c->batch_chunks ? c->batch_chunks : 1, s) != GBU_OK)
+        return GBU_DEVICE_ERROR;
+    return batch_enqueue(c, s);
+}
+
+int32_t gbu_batch_launch_graph(gbu_ctx *c, void *stream)
+{
+    if (!c) return GBU_INVALID_ARG;
+    if (!ok(cudaSetDevice(c->device))) return GBU_DEVICE_ERROR;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (c->batch_items == 0) return GBU_OK;
+    if (c->dirty && ensure_scratch(c, c->batch_chunks, s) != GBU_OK) return GBU_DEVICE_ERROR;
+    if (!c->graph) {
+        if (!c->capture_stream &&
+            !ok(cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking)))
+            return GBU_DEVICE_ERROR;
+        if (job_max_grid(c->device) <= 0) return GBU_DEVICE_ERROR;   // attributes set before capture
+        cudaGraph_t g = nullptr;
+        if (!ok(cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal)))
+            return GBU_DEVICE_ERROR;
+        const int32_t st = batch_enqueue(c, c->capture_stream);
+        const cudaError_t e = cudaStreamEndCapture(c->capture_stream, &g);
+        if (st != GBU_OK || !ok(e) || !g) {
+            if (g) cudaGraphDestroy(g);
+            return GBU_DEVICE_ERROR;
+        }
+        const cudaError_t ie = cudaGraphInstantiate(&c->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (!ok(ie)) {
+            c->graph = nullptr;
+            return GBU_DEVICE_ERROR;
+        }
+    }
+    return ok(cudaGraphLaunch(c->graph, s)) ? GBU_OK : GBU_DEVICE_ERROR;
 }
 
 const char *gbu_status_name(int32_t s)

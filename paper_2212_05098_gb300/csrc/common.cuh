@@ -57,7 +57,7 @@ constexpr uint32_t kStageBytes = kChunkBytes + 2 * kHalo;
 constexpr uint32_t kStage8Units = kChunk8 + 8;
 constexpr uint32_t kStage16Bytes = 3 * kChunk16 + 8;
 constexpr uint32_t kOutBufBytes =
-    (2 * kStage8Units > kStage16Bytes ? 2 * kStage8Units : kStage16Bytes) + 16;
+    (2 * kStage8Units > kStage16Bytes ? 2 * kStage8Units : kStage16Bytes) + 32;
 
 // Status codes (numerically equal to gbu_status in include/gbutf.h).
 enum : int32_t {
@@ -247,9 +247,12 @@ __device__ __forceinline__ uint64_t lookback(const unsigned long long *status, u
     }
 }
 
-// Copy nbytes from shared memory (4-byte aligned, readable 16 bytes past the
+// Copy nbytes from shared memory (16-byte aligned, readable 32 bytes past the
 // end) to global dst with 16-byte aligned vector stores for the body and byte
-// stores at the two unaligned edges. Called by all kThreads threads.
+// stores at the two unaligned edges. Each thread reads two aligned 16-byte
+// blocks of the source and shifts them by the (block-uniform) misalignment,
+// so the shared-memory reads are free of bank conflicts. Called by all
+// kThreads compute threads.
 __device__ __forceinline__ void block_store_bytes(const uint8_t *s_src, uint8_t *dst,
                                                   uint32_t nbytes)
 {
@@ -259,18 +262,23 @@ __device__ __forceinline__ void block_store_bytes(const uint8_t *s_src, uint8_t 
     if (head > nbytes) head = nbytes;
     if (tid < head) dst[tid] = s_src[tid];
     const uint32_t nblk = (nbytes - head) >> 4;
-    const uint32_t *sw = reinterpret_cast<const uint32_t *>(s_src);
+    const uint32_t q = (head >> 2) & 3u, sh = (head & 3u) * 8u;   // same for every block
+    const uint4 *sv = reinterpret_cast<const uint4 *>(s_src);
     for (uint32_t b = tid; b < nblk; b += kThreads) {
-        const uint32_t so = head + 16u * b;
-        const uint32_t *p = sw + (so >> 2);
-        const uint32_t sh = (so & 3u) * 8u;
-        const uint32_t w0 = p[0], w1 = p[1], w2 = p[2], w3 = p[3], w4 = p[4];
+        const uint4 A = sv[b], B = sv[b + 1];                       // bytes 16b .. 16b+31
+        uint32_t x0, x1, x2, x3, x4;
+        switch (q) {
+        case 0: x0 = A.x; x1 = A.y; x2 = A.z; x3 = A.w; x4 = B.x; break;
+        case 1: x0 = A.y; x1 = A.z; x2 = A.w; x3 = B.x; x4 = B.y; break;
+        case 2: x0 = A.z; x1 = A.w; x2 = B.x; x3 = B.y; x4 = B.z; break;
+        default: x0 = A.w; x1 = B.x; x2 = B.y; x3 = B.z; x4 = B.w; break;
+        }
         uint4 v;
-        v.x = __funnelshift_r(w0, w1, sh);
-        v.y = __funnelshift_r(w1, w2, sh);
-        v.z = __funnelshift_r(w2, w3, sh);
-        v.w = __funnelshift_r(w3, w4, sh);
-        *reinterpret_cast<uint4 *>(dst + so) = v;
+        v.x = __funnelshift_r(x0, x1, sh);
+        v.y = __funnelshift_r(x1, x2, sh);
+        v.z = __funnelshift_r(x2, x3, sh);
+        v.w = __funnelshift_r(x3, x4, sh);
+        *reinterpret_cast<uint4 *>(dst + head + 16u * b) = v;
     }
     const uint32_t tail0 = head + 16u * nblk;
     if (tid < nbytes - tail0) dst[tail0 + tid] = s_src[tail0 + tid];

@@ -10,14 +10,13 @@
 //   * the 256 threads classify the chunk (thread t owns bytes [32t, 32t+32)),
 //     count its output, scan the counts across the CTA and publish the
 //     chunk's aggregate for the decoupled look-back;
-//   * the compute threads then assemble the chunk's output into one of two
-//     shared-memory staging buffers;
-//   * a ninth warp looks back for each chunk's offset as soon as its
-//     aggregate is out, waits for the staged output, writes it with 16-byte
-//     stores and frees the buffer.
-// The compute warps thus never wait on a look-back (only on input and on a
-// free staging buffer), and the TMA ring keeps two chunks of input in flight
-// per CTA.
+//   * a ninth warp looks back for the chunk's offset as soon as its aggregate
+//     is out and publishes the inclusive prefix;
+//   * the compute threads assemble the chunk's output into one of two
+//     shared-memory staging buffers and write it out with 16-byte stores two
+//     iterations later, when its offset is long known.
+// The compute warps thus practically never wait on a look-back, and the TMA
+// ring keeps two chunks of input in flight per CTA.
 //
 // Ownership: a UTF-8 unit belongs to the thread holding its end position
 // (see chunk8 below); a UTF-16 surrogate pair belongs to the owner of its
@@ -103,11 +102,17 @@ __device__ __forceinline__ uint32_t spread4(uint32_t m4)
 }
 
 // Exact local rule for every owned position of a flagged thread (rare path).
-// w: 10 words (positions -4 .. 35); end: the 8 end-indicator words. Returns
-// the key of the first error, or ~0.
-__device__ __noinline__ uint64_t first_error_exact8(const uint32_t *w, const uint32_t *end,
-                                                    uint32_t vmask, int64_t pos0, uint32_t t_off)
+// Re-reads the thread's bytes (positions -4 .. 35) from the stage and
+// recomputes the end positions, so the hot path keeps its words in
+// registers. Returns the key of the first error, or ~0.
+__device__ __noinline__ uint64_t first_error_exact8(const uint8_t *stage, int64_t vt, int64_t lo,
+                                                    int64_t hi, uint32_t t_off)
 {
+    const uint8_t *sp = stage + kHalo + 32 * threadIdx.x;
+    uint32_t w[10];
+    for (int j = 0; j < 10; j++)
+        w[j] = mask_word_bytes(*reinterpret_cast<const uint32_t *>(sp - 4 + 4 * j), vt - 4 + 4 * j,
+                               lo, hi);
     uint32_t units = 0;
     for (int i = 0; i < 32; i++) {
         const int j = (i >> 2) + 1;
@@ -115,6 +120,7 @@ __device__ __noinline__ uint64_t first_error_exact8(const uint32_t *w, const uin
         const uint32_t xf = __funnelshift_r(w[j], w[j + 1], sh);   // bytes i .. i+3
         const uint32_t xb = __funnelshift_r(w[j - 1], w[j], sh);   // bytes i-4 .. i-1
         const uint32_t b0 = xf & 0xFFu;
+        const bool valid = vt + i >= lo && vt + i < hi;
         int kind = 0;
         if ((b0 & 0xC0u) == 0x80u) {
             const uint32_t p1 = xb >> 24, p2 = (xb >> 16) & 0xFFu, p3 = (xb >> 8) & 0xFFu;
@@ -144,8 +150,16 @@ __device__ __noinline__ uint64_t first_error_exact8(const uint32_t *w, const uin
                 }
             }
         }
-        if (kind != 0 && ((vmask >> i) & 1u)) return err_key((uint64_t)(pos0 + i), kind, t_off + units);
-        units += (end[i >> 2] >> (8 * (i & 3) + 7)) & 1u;
+        if (kind != 0 && valid) return err_key((uint64_t)(vt + i - lo), kind, t_off + units);
+        // position i ends a unit when the next byte does not continue a
+        // sequence (a continuation expected by a lead at i, i-1 or i-2), or
+        // when i is the third byte of a 4-byte sequence
+        const uint32_t n1 = (xf >> 8) & 0xFFu;                     // byte i+1
+        const uint32_t bm1 = xb >> 24, bm2 = (xb >> 16) & 0xFFu;  // bytes i-1, i-2
+        const bool n1_cont = (n1 & 0xC0u) == 0x80u;
+        const bool expected = b0 >= 0xC0u || bm1 >= 0xE0u || bm2 >= 0xF0u;
+        const bool ends = !(n1_cont && expected) || bm2 >= 0xF0u;
+        if (valid && ends) units++;
     }
     return ~0ull;
 }
@@ -245,11 +259,12 @@ __device__ __forceinline__ uint32_t chunk8_phase1(St8 &st, const uint8_t *stage,
 
 // Exact first error (flagged threads) and staging of the units.
 template <bool kWrite>
-__device__ __forceinline__ void chunk8_phase2(St8 &st, uint8_t *obuf, uint32_t t_off, int64_t vt,
-                                              int64_t lo, unsigned long long *s_err)
+__device__ __forceinline__ void chunk8_phase2(St8 &st, const uint8_t *stage, uint8_t *obuf,
+                                              uint32_t t_off, int64_t vt, int64_t lo, int64_t hi,
+                                              unsigned long long *s_err)
 {
     if (st.bad || st.edge) {
-        const uint64_t key = first_error_exact8(st.w, st.end, st.vmask, vt - lo, t_off);
+        const uint64_t key = first_error_exact8(stage, vt, lo, hi, t_off);
         if (key != ~0ull) atomicMin(s_err, key);
     }
     if (!kWrite) return;
@@ -482,11 +497,10 @@ struct Ring {
     uint32_t chunk[kStages], itidx[kStages], end[kStages];
 };
 
-// Thread 0: claim the next chunk and start its TMA load into `slot`.
+// Thread 0: start the TMA load of chunk c (claimed earlier) into `slot`.
 // Returns false (and marks the slot as the end) when the job is exhausted.
-__device__ __forceinline__ bool produce(const Job &J, int slot, uint8_t *stages, Ring &R)
+__device__ __forceinline__ bool produce(const Job &J, uint32_t c, int slot, uint8_t *stages, Ring &R)
 {
-    const uint32_t c = atomicAdd(J.claim, 1u);
     if (c >= J.total_chunks) {
         R.end[slot] = 1;
         mbar_arrive(&R.full[slot]);
@@ -521,44 +535,57 @@ struct Pending {                 // a processed chunk waiting for its offset
     uint32_t chunk, itidx, agg, end;
 };
 
-// One warp copies nbytes from shared memory (4-byte aligned, readable 16
-// bytes past the end) to global dst: 16-byte aligned vector stores for the
-// body, byte stores at the two unaligned edges.
-__device__ __forceinline__ void warp_store_bytes(const uint8_t *s_src, uint8_t *dst,
-                                                 uint32_t nbytes)
+struct Done {                    // what the look-back warp keeps of a chunk until it is written
+    uint64_t excl;
+    uint32_t chunk, itidx, nchunks;
+};
+
+// The last CTA out checks that every chunk id was handed out exactly once,
+// advances the epoch and resets the job's counters for the next launch.
+__device__ __forceinline__ void exit_job(const Job &J, uint32_t epoch)
 {
-    const uint32_t lane = threadIdx.x & 31;
-    const uintptr_t d = reinterpret_cast<uintptr_t>(dst);
-    uint32_t head = (uint32_t)((16u - (d & 15u)) & 15u);
-    if (head > nbytes) head = nbytes;
-    if (lane < head) dst[lane] = s_src[lane];
-    const uint32_t nblk = (nbytes - head) >> 4;
-    const uint32_t *sw = reinterpret_cast<const uint32_t *>(s_src);
-    for (uint32_t b = lane; b < nblk; b += 32) {
-        const uint32_t so = head + 16u * b;
-        const uint32_t *q = sw + (so >> 2);
-        const uint32_t sh = (so & 3u) * 8u;
-        const uint32_t w0 = q[0], w1 = q[1], w2 = q[2], w3 = q[3], w4 = q[4];
-        uint4 v;
-        v.x = __funnelshift_r(w0, w1, sh);
-        v.y = __funnelshift_r(w1, w2, sh);
-        v.z = __funnelshift_r(w2, w3, sh);
-        v.w = __funnelshift_r(w3, w4, sh);
-        *reinterpret_cast<uint4 *>(dst + so) = v;
+    __threadfence();
+    if (atomicAdd(J.exit_count, 1u) != gridDim.x - 1) return;
+    const unsigned int claims = atomicExch(J.claim, 0u);
+    const unsigned int flags = atomicAdd(J.flags, 0u);
+    if (claims != J.total_chunks + gridDim.x || flags != 0) {
+        // counters were left dirty by an aborted launch, or a wait gave up
+        // (chunks may have been skipped, items left unfinished): no item was
+        // finished reliably
+        const int32_t st = claims != J.total_chunks + gridDim.x || (flags & 2u) ? kDeviceError
+                                                                               : kDeviceTimeout;
+        for (uint32_t it = 0; it < J.num_items; it++) {
+            const Item &X = J.items ? J.items[it] : J.item0;
+            volatile ResultSlot *r = X.result;
+            r->status = st;
+            r->reserved = 0;
+            r->in_offset = 0;
+            r->out_len = 0;
+        }
     }
-    const uint32_t tail0 = head + 16u * nblk;
-    if (lane < nbytes - tail0) dst[tail0 + lane] = s_src[tail0 + lane];
+    const uint32_t next = (epoch + 1) & kEpochMask;
+    if (next == 0)   // wrap: stale words of epoch 0 must not look ready
+        for (uint32_t i = 0; i < J.status_capacity; i++) J.status[i] = 0;
+    *J.epoch = next;
+    *J.exit_count = 0;
+    *J.flags = 0;
+    __threadfence_system();
 }
 
-// Warps 0-7 (compute): per chunk, wait for its stage, classify and count it,
-// scan, publish the aggregate, hand the chunk to the store warp (pend_bar),
-// assemble its output into a staging buffer and signal it (staged_bar). They
-// never wait on a look-back: only on input (full) and on a free staging
-// buffer (free_bar).
-// Warp 8 (look-back and store): per handed-over chunk, look back, publish the
-// inclusive prefix, wait for the staged output, write it at its offset,
-// publish errors, finish the item when it was its last chunk, and free the
-// staging buffer.
+// Warps 0-7 (compute): at iteration i, wait for chunk i's stage, classify and
+// count it, scan, publish its aggregate and hand it to the look-back warp
+// (pend_bar). Then write out chunk i-2 from staging buffer i&1 (its offset was
+// computed meanwhile) and signal it (written_bar), and assemble chunk i's
+// output into the same buffer. Thread 0 also feeds the TMA ring, claiming
+// chunk ids one iteration ahead so that the claim's latency is hidden.
+// Warp 8 (look-back): for every handed-over chunk, as soon as its aggregate
+// is out, look back, publish the inclusive prefix and hand the offset back
+// (excl_bar); once the chunk is written, record its first error and count it
+// done, finishing its item's result when it is the item's last chunk. None of
+// the global atomics and fences of this bookkeeping sit on the compute path.
+// Hand-over slots and their barriers come in fours (chunk j uses j&3): the
+// compute warps may hand over chunk j+2 before the look-back warp took
+// chunk j.
 template <bool kWrite>
 __global__ void __launch_bounds__(kBlock, kMinBlocks)
 transcode_kernel(const Job J)
@@ -567,21 +594,21 @@ transcode_kernel(const Job J)
     uint8_t *const stages = dyn_smem;
     uint8_t *const obufs = dyn_smem + kStages * kStageBytes;
     __shared__ __align__(8) Ring R;
-    __shared__ __align__(8) uint64_t pend_bar[2], staged_bar[2], free_bar[2];
-    __shared__ Pending s_pend[2];
-    __shared__ unsigned long long s_err[2];
+    __shared__ __align__(8) uint64_t pend_bar[4], excl_bar[4], written_bar[4];
+    __shared__ Pending s_pend[4];
+    __shared__ unsigned long long s_excl[4], s_errsnap[4], s_err[2];
     __shared__ uint32_t s_warp[kThreads / 32 + 1];
     __shared__ uint32_t s_epoch;
 
     const uint32_t tid = threadIdx.x;
     if (tid == 0) {
         for (int s = 0; s < kStages; s++) mbar_init(&R.full[s], 1);
-        for (int s = 0; s < 2; s++) {
+        for (int s = 0; s < 4; s++) {
             mbar_init(&pend_bar[s], 1);
-            mbar_init(&staged_bar[s], kThreads);
-            mbar_init(&free_bar[s], 1);
-            s_err[s] = ~0ull;
+            mbar_init(&excl_bar[s], 1);
+            mbar_init(&written_bar[s], 1);
         }
+        s_err[0] = s_err[1] = ~0ull;
         fence_mbar_init();
         s_epoch = *reinterpret_cast<volatile unsigned int *>(J.epoch);
     }
@@ -589,17 +616,33 @@ transcode_kernel(const Job J)
     const uint32_t epoch = s_epoch;
 
     if (tid >= kThreads) {
-        // ---- look-back and store warp -----------------------------------------
+        // ---- look-back warp -------------------------------------------------
         const bool lead = tid == kThreads;
         bool failed = false;
-        for (uint32_t j = 0;; j++) {
-            const int p = j & 1;
-            const uint32_t par = (j >> 1) & 1u;
-            if (!mbar_wait(&pend_bar[p], par)) {
+        Done d1{}, d2{};   // chunks j-1 and j-2
+        // chunk j was written: merge its first error, count it done
+        auto account = [&](const Done &d, uint32_t j) -> bool {
+            if (!mbar_wait(&written_bar[j & 3], (j >> 2) & 1u)) return false;
+            if (lead) {
+                const uint64_t key = s_errsnap[j & 3];
+                if (key != ~0ull) {
+                    J.err_prefix[d.chunk] = d.excl + (key & 0x7FFFu);
+                    atomicMin(&J.item_err[d.itidx], ((key >> 23) << 8) | ((key >> 15) & 0xFFu));
+                }
+                __threadfence();
+                if (atomicAdd(&J.item_done[d.itidx], 1u) == d.nchunks - 1)
+                    finalize_item(J, d.itidx, J.items ? J.items[d.itidx] : J.item0);
+            }
+            return true;
+        };
+        uint32_t j = 0;
+        for (;; j++) {
+            const int q = j & 3;
+            if (!mbar_wait(&pend_bar[q], (j >> 2) & 1u)) {
                 failed = true;
                 break;
             }
-            const Pending &P = s_pend[p];
+            const Pending &P = s_pend[q];
             if (P.end) break;
             const uint32_t k = P.chunk - P.item.chunk_base;
             uint64_t excl = 0;
@@ -608,77 +651,78 @@ transcode_kernel(const Job J)
                 if (lead)
                     st_relaxed(&J.status[P.chunk], pack_status(kFlagInclusive, epoch, excl + P.agg));
             }
-            if (!mbar_wait(&staged_bar[p], par)) {
+            Done d0;
+            d0.excl = excl;
+            d0.chunk = P.chunk;
+            d0.itidx = P.itidx;
+            d0.nchunks = P.item.nchunks;
+            __syncwarp();
+            if (lead) {
+                s_excl[q] = excl;
+                mbar_arrive(&excl_bar[q]);
+            }
+            if (j >= 2 && !account(d2, j - 2)) {
                 failed = true;
                 break;
             }
-            if (kWrite) {
-                const bool u16 = (P.item.op & kOpUtf16) != 0;
-                const uint32_t ub = u16 ? 1u : 2u;                       // output unit bytes
-                const uint32_t stage_units = u16 ? kStage16Bytes : kStage8Units;
-                if (excl < P.item.cap) {
-                    const uint64_t room = P.item.cap - excl;
-                    uint32_t nw = P.agg < stage_units ? P.agg : stage_units;
-                    if (nw > room) nw = (uint32_t)room;
-                    warp_store_bytes(obufs + (size_t)p * kOutBufBytes, P.item.out + excl * ub, nw * ub);
-                }
-            }
-            if (lead) {
-                const uint64_t key = s_err[p];
-                if (key != ~0ull) {
-                    J.err_prefix[P.chunk] = excl + (key & 0x7FFFu);
-                    atomicMin(&J.item_err[P.itidx], ((key >> 23) << 8) | ((key >> 15) & 0xFFu));
-                    s_err[p] = ~0ull;
-                }
-                __threadfence();
-                if (atomicAdd(&J.item_done[P.itidx], 1u) == P.item.nchunks - 1)
-                    finalize_item(J, P.itidx, P.item);
-            }
-            __syncwarp();
-            if (lead) mbar_arrive(&free_bar[p]);
+            d2 = d1;
+            d1 = d0;
         }
-        // last CTA out: check that every chunk id was handed out exactly once,
-        // advance the epoch, and reset the job's counters for the next launch
+        // the compute warps stop after writing out the last two chunks
+        if (!failed && j >= 2 && !account(d2, j - 2)) failed = true;
+        if (!failed && j >= 1 && !account(d1, j - 1)) failed = true;
         if (lead) {
             if (failed) atomicOr(J.flags, 1u);
-            __threadfence();
-            if (atomicAdd(J.exit_count, 1u) == gridDim.x - 1) {
-                const unsigned int claims = atomicExch(J.claim, 0u);
-                if (claims != J.total_chunks + gridDim.x) {
-                    // counters were left dirty by an aborted launch: no item
-                    // was finished reliably
-                    for (uint32_t it = 0; it < J.num_items; it++) {
-                        const Item &X = J.items ? J.items[it] : J.item0;
-                        volatile ResultSlot *r = X.result;
-                        r->status = kDeviceError;
-                        r->reserved = 0;
-                        r->in_offset = 0;
-                        r->out_len = 0;
-                    }
-                }
-                const uint32_t next = (epoch + 1) & kEpochMask;
-                if (next == 0)   // wrap: stale words of epoch 0 must not look ready
-                    for (uint32_t i = 0; i < J.status_capacity; i++) J.status[i] = 0;
-                *J.epoch = next;
-                *J.exit_count = 0;
-                *J.flags = 0;
-                __threadfence_system();
-            }
+            exit_job(J, epoch);
         }
         return;
     }
 
     // ---- compute warps ------------------------------------------------------
-    bool producing = true;   // meaningful in thread 0 only
-    if (tid == 0)
-        for (int s = 0; s < kStages - 1 && producing; s++) producing = produce(J, s, stages, R);
+    // write out chunk j (staging buffer j&1) once its offset is known; false
+    // if the wait for the offset gave up
+    auto write_out = [&](uint32_t j) -> bool {
+        const int q = j & 3;
+        if (!mbar_wait(&excl_bar[q], (j >> 2) & 1u)) return false;
+        if (kWrite) {
+            const Pending &P = s_pend[q];
+            const uint64_t excl = s_excl[q];
+            const bool u16 = (P.item.op & kOpUtf16) != 0;
+            const uint32_t ub = u16 ? 1u : 2u;                       // output unit bytes
+            const uint32_t stage_units = u16 ? kStage16Bytes : kStage8Units;
+            if (excl < P.item.cap) {
+                const uint64_t room = P.item.cap - excl;
+                uint32_t nw = P.agg < stage_units ? P.agg : stage_units;
+                if (nw > room) nw = (uint32_t)room;
+                block_store_bytes(obufs + (size_t)(j & 1) * kOutBufBytes, P.item.out + excl * ub,
+                                  nw * ub);
+            }
+        }
+        if (tid == 0) {
+            s_errsnap[q] = s_err[j & 1];
+            s_err[j & 1] = ~0ull;
+            mbar_arrive(&written_bar[q]);
+        }
+        return true;
+    };
 
-    uint32_t iter = 0;
+    bool producing = true;   // meaningful in thread 0 only
+    uint32_t next_claim = 0;
+    if (tid == 0) {
+        for (int s = 0; s < kStages - 1 && producing; s++)
+            producing = produce(J, atomicAdd(J.claim, 1u), s, stages, R);
+        if (producing) next_claim = atomicAdd(J.claim, 1u);
+    }
+
+    uint32_t iter = 0, handed = 0;
     bool failed = false;
     while (true) {
         const int slot = iter % kStages;
         const int p = iter & 1;
-        if (tid == 0 && producing) producing = produce(J, (iter + kStages - 1) % kStages, stages, R);
+        if (tid == 0 && producing) {
+            producing = produce(J, next_claim, (iter + kStages - 1) % kStages, stages, R);
+            if (producing) next_claim = atomicAdd(J.claim, 1u);   // used next iteration
+        }
         const bool ok = mbar_wait(&R.full[slot], (iter / kStages) & 1u);
         if (cw_sync_or(!ok)) {
             failed = true;
@@ -693,53 +737,53 @@ transcode_kernel(const Job J)
         const int64_t lo = I.head, hi = (int64_t)I.head + (int64_t)I.n;
         const uint32_t k = c - I.chunk_base;
         uint32_t agg, t_off;
-        // publish the aggregate, wait until the store warp is done with this
-        // staging buffer (chunk iter-2), then hand the chunk over
-        auto hand_over = [&]() -> bool {
-            if (tid == 0)
-                st_relaxed(&J.status[c], pack_status(k == 0 ? kFlagInclusive : kFlagAggregate, epoch, agg));
-            if (iter >= 2 && !mbar_wait(&free_bar[p], ((iter - 2) >> 1) & 1u)) return false;
+        auto hand_over = [&]() {
             if (tid == 0) {
-                Pending &P = s_pend[p];
+                st_relaxed(&J.status[c], pack_status(k == 0 ? kFlagInclusive : kFlagAggregate, epoch, agg));
+                Pending &P = s_pend[iter & 3];
                 P.item = I;
                 P.chunk = c;
                 P.itidx = it;
                 P.agg = agg;
                 P.end = 0;
-                mbar_arrive(&pend_bar[p]);
+                mbar_arrive(&pend_bar[iter & 3]);
             }
-            return true;
+            handed++;
         };
-        bool ok2;
         if (I.op & kOpUtf16) {
             const int64_t vt = (int64_t)k * kChunk16 + 16 * tid;
             St16 st;
             const uint32_t cnt = chunk16_phase1(st, stage, vt, lo, hi);
             t_off = block_exclusive_scan(cnt, s_warp, &agg);
-            ok2 = hand_over();
-            if (ok2) chunk16_phase2<kWrite>(st, obuf, t_off, vt, lo, &s_err[p]);
+            hand_over();
+            if (iter >= 2 && cw_sync_or(!write_out(iter - 2))) {
+                failed = true;
+                break;
+            }
+            chunk16_phase2<kWrite>(st, obuf, t_off, vt, lo, &s_err[p]);
         } else {
             const int64_t vt = (int64_t)k * kChunk8 + 32 * tid;
             St8 st;
             const uint32_t cnt = chunk8_phase1(st, stage, vt, lo, hi);
             t_off = block_exclusive_scan(cnt, s_warp, &agg);
-            ok2 = hand_over();
-            if (ok2) chunk8_phase2<kWrite>(st, obuf, t_off, vt, lo, &s_err[p]);
+            hand_over();
+            if (iter >= 2 && cw_sync_or(!write_out(iter - 2))) {
+                failed = true;
+                break;
+            }
+            chunk8_phase2<kWrite>(st, stage, obuf, t_off, vt, lo, hi, &s_err[p]);
         }
-        mbar_arrive(&staged_bar[p]);
-        if (cw_sync_or(!ok2)) {
-            failed = true;
-            break;
-        }
+        cw_sync();
         iter++;
     }
-    // stop the store warp once it is done with chunk iter-2's buffer
+    // drain: write out the last two chunks, then stop the look-back warp
+    if (!failed && iter >= 2 && cw_sync_or(!write_out(iter - 2))) failed = true;
+    if (!failed && iter >= 1 && cw_sync_or(!write_out(iter - 1))) failed = true;
     if (tid == 0) {
         if (failed) atomicOr(J.flags, 1u);
-        if (iter >= 2) mbar_wait(&free_bar[iter & 1], ((iter - 2) >> 1) & 1u);
-        Pending &P = s_pend[iter & 1];
+        Pending &P = s_pend[handed & 3];
         P.end = 1;
-        mbar_arrive(&pend_bar[iter & 1]);
+        mbar_arrive(&pend_bar[handed & 3]);
     }
 }
 

@@ -94,18 +94,20 @@ def source_hash(kernel: str) -> str:
 
 
 def traffic_record(kernel: str):
-    """DRAM bytes per input byte from the committed ncu summary, if it was
-    taken on the kernel source as it is now (else None)."""
+    """DRAM bytes per algorithmic byte, per "profile/direction", from the
+    committed ncu summary, if it was taken on the kernel source as it is now
+    (else {})."""
     p = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     if not os.path.exists(p):
-        return None
+        return {}
     want = source_hash(kernel)
+    out = {}
     with open(p) as f:
         for line in f:
             parts = line.split()
             if len(parts) >= 4 and not line.startswith("#") and parts[0] == kernel and parts[1] == want:
-                return float(parts[3])   # dram bytes per input byte
-    return None
+                out[parts[2]] = float(parts[3])
+    return out
 
 
 class ClockSampler:
@@ -342,7 +344,10 @@ def main():
     tot_bytes = sum(x["bytes"] for x in per_dir.values())
     tot_in = sum(x["in_bytes"] for x in per_dir.values())
     n_launch = sum(x["launches"] for x in per_dir.values())
-    ratio = traffic_record(KERNEL)
+    ratios = traffic_record(KERNEL)
+    traffic = None
+    if all(f"{c['profile']}/{c['dir']}" in ratios for c in cases):
+        traffic = sum(ratios[f"{c['profile']}/{c['dir']}"] * c["alg_bytes"] for c in cases) / len(cases)
     achieved = tot_bytes / (tot_ms / 1e3) / 1e9
     directions = {dname: {"achieved_gbs": d["bytes"] / (d["ms"] / 1e3) / 1e9,
                           "frac": d["bytes"] / (d["ms"] / 1e3) / 1e9 / peak,
@@ -352,7 +357,7 @@ def main():
                   for dname, d in per_dir.items()}
     roofline = {"kernel": KERNEL, "bound": "hbm", "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak,
-                "traffic": (ratio * tot_in / n_launch) if ratio else None,
+                "traffic": traffic,
                 "peak_source": peak_src,
                 "algorithmic_bytes_per_launch": tot_bytes / n_launch,
                 "avg_launch_ms": tot_ms / n_launch}
@@ -412,7 +417,9 @@ def main():
             "config": {"workload": WORKLOAD, "bytes_per_buffer": args.size,
                        "buffers": len(cases), "profiles": profiles,
                        "parallelism": f"independent buffers per rank x {world}",
-                       "l2": "inputs 1 GiB each, larger than the 129 MB L2; no flush"},
+                       "l2": f"inputs {args.size >> 20} MiB each"
+                             + (", larger than the 129 MB L2; no flush" if args.size > (129 << 20)
+                                else ", NOT larger than L2 (profiling case only)")},
             "roofline": roofline,
             "directions": directions,
             "per_buffer_input_gbs": per_case,

@@ -63,6 +63,13 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=256 << 20,
                     help="bytes of each buffer the oracle baseline transcodes")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", choices=["single", "batched"], default="single",
+                    help="single: 4 profiles x 2 directions x one buffer each (default); "
+                         "batched: many strings in one persistent graph-captured launch")
+    ap.add_argument("--strings", type=int, default=200_000, help="batched: number of strings")
+    ap.add_argument("--batch-total", type=int, default=0,
+                    help="batched: scale the string lengths so that they add up to this many "
+                         "bytes (0: unscaled, log-uniform 16 B - 1 MiB)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -235,6 +242,9 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "batched":
+        run_batched(args, rank, world, local)
         return
     # process pool for the generator: started before the first CUDA call
     pool = textgen.process_pool() if args.size >= (64 << 20) else None
@@ -429,6 +439,210 @@ def main():
             "gpu_launches": launches,
         }
         print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+BATCH_METRIC = ("input GB/s, validated UTF-8<->UTF-16LE transcoding of many strings in one "
+                "persistent graph-captured launch")
+
+
+def run_batched(args, rank, world, local):
+    """Batched workload: `--strings` independent strings, lengths log-uniform
+    over 16 B - 1 MiB (optionally scaled to `--batch-total` bytes), profile
+    uniform over the four, direction 50/50, each a window of that profile's
+    corpus (`--size` bytes per profile and encoding) cut at character
+    boundaries. One step = one launch of the autotuned batch (CUDA graph).
+    Also timed in the same run: the same strings as one plain-kernel launch
+    each, and the plain single-buffer kernel on the corpora themselves."""
+    from textgen import batch as tbatch
+    pool = textgen.process_pool()
+    import torch
+    import torch.distributed as dist
+
+    import paper_2212_05098_gb300 as gbu
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    profiles = args.profiles.split(",")
+    cases = gen_inputs(profiles, args.size, rank, pool)
+    pool.shutdown()
+    corpora = [(c["profile"], textgen.UTF8 if c["dir"] == "utf8_to_utf16le" else textgen.UTF16,
+                c["data"]) for c in cases]
+    lay = tbatch.layout(corpora, args.strings, 16, 1 << 20, seed=4 + 1000 * rank)
+    if args.batch_total:
+        lay = tbatch.layout(corpora, args.strings, 16, 1 << 20, seed=4 + 1000 * rank,
+                            scale=args.batch_total / lay.total_bytes)
+    n_str = lay.nbytes.size
+
+    gbu.load()
+    d_corp = [torch.from_numpy(c["data"]).cuda() for c in cases]
+    is16 = np.array([corpora[k][1] == textgen.UTF16 for k in lay.corpus])
+    cap_bytes = np.where(is16, 3 * (lay.nbytes // 2), 2 * lay.nbytes)
+    out_off = np.zeros(n_str + 1, dtype=np.int64)
+    np.cumsum((cap_bytes + 15) // 16 * 16, out=out_off[1:])
+    d_out = torch.empty(int(out_off[-1]) + 16, dtype=torch.uint8, device="cuda")
+    d_res = torch.zeros(n_str * 24, dtype=torch.uint8, device="cuda")
+    base_out = d_out.data_ptr()
+    items = []
+    for i in range(n_str):
+        k = int(lay.corpus[i])
+        inp = d_corp[k].data_ptr() + int(lay.start[i])
+        if is16[i]:
+            n = int(lay.nbytes[i]) // 2
+            items.append((inp if n else 0, n, base_out + int(out_off[i]), 3 * n,
+                          gbu.GBU_OP_UTF16LE_TO_UTF8))
+        else:
+            n = int(lay.nbytes[i])
+            items.append((inp if n else 0, n, base_out + int(out_off[i]), n,
+                          gbu.GBU_OP_UTF8_TO_UTF16LE))
+    ctx = gbu.Context(local)
+    stream = torch.cuda.Stream()
+    sh = stream.cuda_stream
+    st = gbu.gbu_batch_plan(ctx.handle, items, d_res.data_ptr(), sh)
+    if st != gbu.GBU_OK:
+        raise RuntimeError(f"batch plan: {gbu.status_name(st)}")
+    cache = os.path.join(ROOT, "paper_2212_05098_gb300", "_build", "tune_cache.txt")
+    t_tune0 = time.perf_counter()
+    st, tune = gbu.gbu_batch_autotune(ctx.handle, sh, cache)
+    t_tune = time.perf_counter() - t_tune0
+    if st != gbu.GBU_OK:
+        raise RuntimeError(f"autotune: {gbu.status_name(st)}")
+    for _ in range(max(3, args.warmup)):
+        if gbu.gbu_batch_launch_graph(ctx.handle, sh) != gbu.GBU_OK:
+            raise RuntimeError("batch launch failed")
+    stream.synchronize()
+    res = np.frombuffer(d_res.cpu().numpy().tobytes(),
+                        dtype=[("status", "<i4"), ("r", "<u4"), ("off", "<u8"), ("len", "<u8")])
+    if (res["status"] != 0).any():
+        i = int(np.nonzero(res["status"] != 0)[0][0])
+        raise RuntimeError(f"string {i}: {gbu.status_name(int(res['status'][i]))}")
+    in_bytes = int(lay.nbytes.sum())
+    out_bytes = int((res["len"] * np.where(is16, 1, 2)).sum())
+
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(K)]
+    sampler = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    n0 = gbu.gbu_kernel_launch_count()
+    t_wall0 = time.time()
+    for k in range(K):
+        ev[k][0].record(stream)
+        gbu.gbu_batch_launch_graph(ctx.handle, sh)
+        ev[k][1].record(stream)
+    stream.synchronize()
+    t_wall1 = time.time()
+    launches = gbu.gbu_kernel_launch_count() - n0
+    sampler.stop()
+    clocks = sampler.summary(t_wall0, t_wall1)
+    ms_list = [a.elapsed_time(b) for a, b in ev]
+    ms = torch.tensor([sum(ms_list)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(ms, op=dist.ReduceOp.MAX)
+    ms_total = float(ms.item())
+    value = world * in_bytes * K / (ms_total / 1e3) / 1e9
+
+    # the same strings, one plain-kernel launch each (default launch parameters)
+    plain = gbu.Context(local)
+    plain.reserve(1 << 20)
+    res1 = torch.zeros(4, dtype=torch.int64, device="cuda")
+    r1 = res1.data_ptr()
+
+    def per_string():
+        for (inp, n, outp, cap, op) in items:
+            if op == gbu.GBU_OP_UTF8_TO_UTF16LE:
+                gbu.gbu_utf8_to_utf16le_async(plain.handle, inp, n, outp, cap, r1, sh)
+            else:
+                gbu.gbu_utf16le_to_utf8_async(plain.handle, inp, n, outp, cap, r1, sh)
+
+    per_string()
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record(stream)
+    per_string()
+    e1.record(stream)
+    stream.synchronize()
+    ps_wall = time.perf_counter() - t0
+    ps_ms = e0.elapsed_time(e1)
+
+    # the plain single-buffer kernel on the corpora (same GPU, same run)
+    def single():
+        for c, d in zip(cases, d_corp):
+            if c["dir"] == "utf8_to_utf16le":
+                gbu.gbu_utf8_to_utf16le_async(plain.handle, d.data_ptr(), d.numel(),
+                                              d_out.data_ptr(), d.numel(), r1, sh)
+            else:
+                gbu.gbu_utf16le_to_utf8_async(plain.handle, d.data_ptr(), d.numel() // 2,
+                                              d_out.data_ptr(), 3 * (d.numel() // 2), r1, sh)
+
+    plain.reserve(args.size)
+    single()
+    e0.record(stream)
+    for _ in range(3):
+        single()
+    e1.record(stream)
+    stream.synchronize()
+    single_gbs = 3 * sum(d.numel() for d in d_corp) / (e0.elapsed_time(e1) / 1e3) / 1e9
+
+    peak, peak_src = measured_peak()
+    ms_launch = ms_total / K
+    roofline = {"kernel": KERNEL, "bound": "hbm",
+                "achieved": (in_bytes + out_bytes) / (ms_launch / 1e3) / 1e9, "peak": peak,
+                "unit": "GB/s", "frac": (in_bytes + out_bytes) / (ms_launch / 1e3) / 1e9 / peak,
+                "traffic": None, "peak_source": peak_src,
+                "algorithmic_bytes_per_launch": in_bytes + out_bytes, "avg_launch_ms": ms_launch}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        budget, done, t_c = args.cpu_sample, 0, 0.0
+        for i in range(n_str):
+            if done >= budget:
+                break
+            d = cases[int(lay.corpus[i])]["data"][int(lay.start[i]):int(lay.start[i] + lay.nbytes[i])]
+            t0 = time.perf_counter()
+            if is16[i]:
+                oracle.utf16le_to_utf8(d)
+            else:
+                oracle.utf8_to_utf16le(d)
+            t_c += time.perf_counter() - t0
+            done += d.size
+        cpu = {"value": done / t_c / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": f"oracle (scalar C, 1 thread) on the first strings of the batch, "
+                         f"{done / 1e9:.2f} GB, {t_c:.1f} s"}
+    if rank == 0:
+        line = {
+            "metric": BATCH_METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
+            "steps": K, "warmup": max(3, args.warmup), "ms_per_step": ms_total / K,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u8+u16", "data": "synthetic (windows of seeded per-profile corpora)",
+            "config": {"workload": f"{n_str} strings, lengths log-uniform 16 B-1 MiB"
+                                   + (f" scaled to {args.batch_total} B total" if args.batch_total
+                                      else "")
+                                   + ", profiles uniform over 4, direction 50/50",
+                       "strings": n_str, "input_bytes": in_bytes, "output_bytes": out_bytes,
+                       "corpus_bytes_per_profile_and_encoding": args.size,
+                       "tune": {"look_width": tune.look_width, "ctas_per_sm": tune.ctas_per_sm,
+                                "autotune_s": round(t_tune, 3)},
+                       "l2": "inputs read once per step from 8 corpora of "
+                             f"{args.size >> 20} MiB; no flush"},
+            "roofline": roofline,
+            "per_string_launches": {"value": in_bytes / (ps_ms / 1e3) / 1e9, "unit": "GB/s",
+                                    "ms": ps_ms, "host_s": ps_wall, "launches": n_str},
+            "plain_single_buffer_gbs": single_gbs,
+            "plain_over_batched": single_gbs / value * world,
+            "cpu_baseline": cpu,
+            "e2e": None,
+            "clocks": clocks,
+            "gpu_launches": launches,
+        }
+        print(json.dumps(line), flush=True)
+    plain.close()
     ctx.close()
     if world > 1:
         dist.destroy_process_group()

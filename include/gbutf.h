@@ -142,8 +142,9 @@ gbu_result gbu_utf16le_to_utf8_host(gbu_ctx *ctx, const uint16_t *h_in, uint64_t
  *
  * The paper transcodes one buffer per call; a batch runs many such calls (any
  * mix of directions and of transcoding / length-only) in ONE launch of the
- * persistent kernel: the chunks of all inputs are numbered consecutively and
- * handed out in order, every input keeps its own prefix scan, first error and
+ * persistent kernel: the chunks of all inputs are numbered consecutively
+ * (grouped by operation, in item order within a group) and handed out in
+ * order, every input keeps its own prefix scan, first error and
  * result, so each result equals that of the single-buffer call on the same
  * input. */
 typedef enum gbu_op {
@@ -181,6 +182,34 @@ int32_t gbu_batch_launch(gbu_ctx *ctx, void *stream);
 /* Same, through a CUDA graph the context captures once per plan and replays
  * on `stream` (lowest launch overhead for repeated batches). */
 int32_t gbu_batch_launch_graph(gbu_ctx *ctx, void *stream);
+
+/* Launch parameters of a context (a tuning, not part of the paper's method:
+ * results never depend on them). look_width: status words each lane of the
+ * look-back warp reads per round (4, 8 or 16; the 32 * look_width nearest
+ * predecessors per round). ctas_per_sm: resident CTAs per SM of the
+ * persistent grid (0: as many as fit, 1..that maximum otherwise). */
+typedef struct gbu_tune {
+    int32_t look_width;
+    int32_t ctas_per_sm;
+} gbu_tune;
+
+/* Read / set the context's launch parameters (default {8, 0}). Setting them
+ * drops the context's captured batch graph. GBU_INVALID_ARG for values
+ * outside the ranges above. */
+int32_t gbu_get_tune(gbu_ctx *ctx, gbu_tune *tune);
+int32_t gbu_set_tune(gbu_ctx *ctx, const gbu_tune *tune);
+
+/* Autotune the planned batch: time one warm-up and three launches of it on
+ * `stream` for every (look_width, ctas_per_sm) pair, keep the pair with the
+ * lowest median time on the context and store it in *chosen (may be NULL).
+ * The batch's outputs and results are written by every timed launch (the
+ * same values each time). If `cache_path` is not NULL, a text file of lines
+ * "<key> <look_width> <ctas_per_sm> <ms>" is consulted first (key: device
+ * name, SM count, and the batch's item count and input bytes in powers of two
+ * and UTF-16 / transcoding shares in tenths) and the new choice is appended
+ * to it; a cached key skips the timing. Blocks until done. Returns GBU_OK,
+ * GBU_INVALID_ARG or GBU_DEVICE_ERROR (a failing launch). */
+int32_t gbu_batch_autotune(gbu_ctx *ctx, void *stream, const char *cache_path, gbu_tune *chosen);
 
 /* No-allocation form of gbu_utf8_to_utf16le. The paper has no counterpart to
  * this call: it is for callers that may not allocate device memory (another

@@ -63,6 +63,10 @@ class gbu_batch_item(ctypes.Structure):
                 ("cap", ctypes.c_uint64), ("op", ctypes.c_int32), ("reserved", ctypes.c_uint32)]
 
 
+class gbu_tune(ctypes.Structure):
+    _fields_ = [("look_width", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
+
+
 # name -> (restype, argtypes)
 _VP, _U64, _I32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int32
 _RP = ctypes.POINTER(gbu_result)
@@ -83,6 +87,9 @@ SIGNATURES = {
     "gbu_batch_plan": (_I32, [_VP, ctypes.POINTER(gbu_batch_item), ctypes.c_uint32, _VP, _VP]),
     "gbu_batch_launch": (_I32, [_VP, _VP]),
     "gbu_batch_launch_graph": (_I32, [_VP, _VP]),
+    "gbu_get_tune": (_I32, [_VP, ctypes.POINTER(gbu_tune)]),
+    "gbu_set_tune": (_I32, [_VP, ctypes.POINTER(gbu_tune)]),
+    "gbu_batch_autotune": (_I32, [_VP, _VP, ctypes.c_char_p, ctypes.POINTER(gbu_tune)]),
     "gbu_utf8_to_utf16le_noalloc": (gbu_result, [_VP, _U64, _VP, _U64, _VP]),
     "gbu_status_name": (ctypes.c_char_p, [_I32]),
     "gbu_kernel_launch_count": (_U64, []),
@@ -186,6 +193,27 @@ def gbu_batch_launch(ctx, stream=0) -> int:
 
 def gbu_batch_launch_graph(ctx, stream=0) -> int:
     return load().gbu_batch_launch_graph(ctx, stream)
+
+
+def gbu_get_tune(ctx) -> gbu_tune:
+    t = gbu_tune()
+    st = load().gbu_get_tune(ctx, ctypes.byref(t))
+    if st != GBU_OK:
+        raise RuntimeError(status_name(st))
+    return t
+
+
+def gbu_set_tune(ctx, look_width: int, ctas_per_sm: int) -> int:
+    t = gbu_tune(look_width, ctas_per_sm)
+    return load().gbu_set_tune(ctx, ctypes.byref(t))
+
+
+def gbu_batch_autotune(ctx, stream=0, cache_path: str | None = None):
+    """Returns (status, gbu_tune chosen)."""
+    t = gbu_tune()
+    path = cache_path.encode() if cache_path else None
+    st = load().gbu_batch_autotune(ctx, stream, path, ctypes.byref(t))
+    return st, t
 
 
 def gbu_utf8_to_utf16le_noalloc(d_in, n_bytes, d_out, cap_units, stream=0) -> Result:

@@ -1,12 +1,16 @@
 // C ABI of the library (declared in include/gbutf.h): contexts, scratch
-// management and the synchronous / asynchronous / host-buffer entry points.
-// Every step of the transcoding runs in the kernels of utf8_to_utf16.cu and
-// utf16_to_utf8.cu; this file only validates arguments, sizes scratch and
-// enqueues work.
+// management, the synchronous / asynchronous / host-buffer entry points, the
+// batch calls and their autotuner. Every step of the transcoding runs in the
+// kernel of transcode.cu; this file only validates arguments, sizes scratch,
+// enqueues work and times launches.
+#include <algorithm>
 #include <atomic>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <string>
+#include <vector>
 
 #include "../../include/gbutf.h"
 #include "kernels.h"
@@ -55,6 +59,7 @@ struct gbu_ctx {
     bool batch_write = false;
     cudaStream_t capture_stream = nullptr;
     cudaGraphExec_t graph = nullptr;
+    gbu::Tune tune;                   // launch parameters of every call on the context
 };
 
 namespace {
@@ -134,10 +139,10 @@ int32_t enqueue(gbu_ctx *c, Op op, const void *in, uint64_t n, void *out, uint64
         return st;
     }
     attach_scratch(c, J);
-    int grid = job_max_grid(c->device);
+    int grid = job_grid(c->device, c->tune);
     if (grid <= 0) return GBU_DEVICE_ERROR;
     if ((uint32_t)grid > J.total_chunks) grid = (int)J.total_chunks;
-    const cudaError_t e = launch_job(J, write, grid, stream);
+    const cudaError_t e = launch_job(J, write, grid, stream, c->tune.look);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     if (!ok(e)) {
         c->dirty = true;
@@ -381,16 +386,22 @@ int32_t gbu_batch_plan(gbu_ctx *c, const gbu_batch_item *items, uint32_t count,
     if (chunks >= (1ull << 32)) return GBU_INVALID_ARG;
     if (!ok(cudaStreamSynchronize(s))) return GBU_DEVICE_ERROR;   // host staging is reused
     if (!grow_batch(c, count ? count : 1, chunks ? chunks : 1)) return GBU_DEVICE_ERROR;
+    // Chunks are numbered operation by operation (items keep their index and
+    // result slot): a CTA then mostly runs one code path at a time, which
+    // keeps the instruction cache warm.
     uint32_t base = 0;
-    for (uint32_t i = 0; i < count; i++) {
-        const gbu_batch_item &b = items[i];
-        const bool utf16 = b.op == GBU_OP_UTF16LE_TO_UTF8 || b.op == GBU_OP_UTF8_LENGTH_FROM_UTF16LE;
-        const bool write = b.op <= GBU_OP_UTF16LE_TO_UTF8;
-        Item I = make_item(b.in, b.n, utf16, b.out, b.cap, write,
-                           reinterpret_cast<ResultSlot *>(results + i), base);
-        c->h_items[i] = I;
-        for (uint32_t k = 0; k < I.nchunks; k++) c->h_chunk_item[base + k] = i;
-        base += I.nchunks;
+    for (int op = GBU_OP_UTF8_TO_UTF16LE; op <= GBU_OP_UTF8_LENGTH_FROM_UTF16LE; op++) {
+        for (uint32_t i = 0; i < count; i++) {
+            const gbu_batch_item &b = items[i];
+            if (b.op != op) continue;
+            const bool utf16 = b.op == GBU_OP_UTF16LE_TO_UTF8 || b.op == GBU_OP_UTF8_LENGTH_FROM_UTF16LE;
+            const bool write = b.op <= GBU_OP_UTF16LE_TO_UTF8;
+            Item I = make_item(b.in, b.n, utf16, b.out, b.cap, write,
+                               reinterpret_cast<ResultSlot *>(results + i), base);
+            c->h_items[i] = I;
+            for (uint32_t k = 0; k < I.nchunks; k++) c->h_chunk_item[base + k] = i;
+            base += I.nchunks;
+        }
     }
     int32_t st = ensure_scratch(c, chunks ? chunks : 1, s);
     if (st != GBU_OK) return st;
@@ -412,7 +423,8 @@ int32_t gbu_batch_plan(gbu_ctx *c, const gbu_batch_item *items, uint32_t count,
     return GBU_OK;
 }
 
-static int32_t batch_enqueue(gbu_ctx *c, cudaStream_t s)
+// Enqueue the planned batch; `counted`: a real launch (not a graph capture).
+static int32_t batch_enqueue(gbu_ctx *c, cudaStream_t s, bool counted = true)
 {
     if (c->batch_items == 0) return GBU_OK;
     Job J{};
@@ -423,11 +435,11 @@ static int32_t batch_enqueue(gbu_ctx *c, cudaStream_t s)
     attach_scratch(c, J);
     J.item_err = c->d_item_err;
     J.item_done = c->d_item_done;
-    int grid = job_max_grid(c->device);
+    int grid = job_grid(c->device, c->tune);
     if (grid <= 0) return GBU_DEVICE_ERROR;
     if ((uint32_t)grid > J.total_chunks) grid = (int)J.total_chunks;
-    const cudaError_t e = launch_job(J, c->batch_write, grid, s);
-    g_launches.fetch_add(1, std::memory_order_relaxed);
+    const cudaError_t e = launch_job(J, c->batch_write, grid, s, c->tune.look);
+    if (counted) g_launches.fetch_add(1, std::memory_order_relaxed);
     return ok(e) ? GBU_OK : GBU_DEVICE_ERROR;
 }
 
@@ -456,7 +468,7 @@ int32_t gbu_batch_launch_graph(gbu_ctx *c, void *stream)
         cudaGraph_t g = nullptr;
         if (!ok(cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal)))
             return GBU_DEVICE_ERROR;
-        const int32_t st = batch_enqueue(c, c->capture_stream);
+        const int32_t st = batch_enqueue(c, c->capture_stream, false);
         const cudaError_t e = cudaStreamEndCapture(c->capture_stream, &g);
         if (st != GBU_OK || !ok(e) || !g) {
             if (g) cudaGraphDestroy(g);
@@ -469,7 +481,165 @@ int32_t gbu_batch_launch_graph(gbu_ctx *c, void *stream)
             return GBU_DEVICE_ERROR;
         }
     }
-    return ok(cudaGraphLaunch(c->graph, s)) ? GBU_OK : GBU_DEVICE_ERROR;
+    if (!ok(cudaGraphLaunch(c->graph, s))) return GBU_DEVICE_ERROR;
+    g_launches.fetch_add(1, std::memory_order_relaxed);   // the graph holds one kernel launch
+    return GBU_OK;
+}
+
+int32_t gbu_get_tune(gbu_ctx *c, gbu_tune *t)
+{
+    if (!c || !t) return GBU_INVALID_ARG;
+    t->look_width = c->tune.look;
+    t->ctas_per_sm = c->tune.ctas_per_sm;
+    return GBU_OK;
+}
+
+int32_t gbu_set_tune(gbu_ctx *c, const gbu_tune *t)
+{
+    if (!c || !t) return GBU_INVALID_ARG;
+    bool known = false;
+    for (const int w : kLookWidths) known |= w == t->look_width;
+    if (!known || t->ctas_per_sm < 0) return GBU_INVALID_ARG;
+    if (!ok(cudaSetDevice(c->device))) return GBU_DEVICE_ERROR;
+    const int per = job_max_ctas_per_sm(c->device);
+    if (per <= 0) return GBU_DEVICE_ERROR;
+    if (t->ctas_per_sm > per) return GBU_INVALID_ARG;
+    if (c->tune.look != t->look_width || c->tune.ctas_per_sm != t->ctas_per_sm) {
+        c->tune.look = t->look_width;
+        c->tune.ctas_per_sm = t->ctas_per_sm;
+        if (c->graph) {   // the captured launch has the old parameters
+            cudaGraphExecDestroy(c->graph);
+            c->graph = nullptr;
+        }
+    }
+    return GBU_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Cache key of a planned batch on this device: the device, and the batch's
+// shape in coarse buckets (item count and input bytes by powers of two, the
+// UTF-16 and writing shares by tenths).
+std::string tune_key(gbu_ctx *c)
+{
+    cudaDeviceProp prop{};
+    if (!ok(cudaGetDeviceProperties(&prop, c->device))) return std::string();
+    uint64_t bytes = 0;
+    uint32_t u16 = 0, wr = 0;
+    for (uint32_t i = 0; i < c->batch_items; i++) {
+        const Item &I = c->h_items[i];
+        const bool is16 = (I.op & kOpUtf16) != 0;
+        bytes += I.n * (is16 ? 2 : 1);
+        u16 += is16;
+        wr += (I.op & kOpWrite) != 0;
+    }
+    char buf[384];
+    std::string name(prop.name);
+    std::replace(name.begin(), name.end(), ' ', '_');
+    const int items_b = (int)std::floor(std::log2((double)c->batch_items + 1));
+    const int bytes_b = (int)std::floor(std::log2((double)bytes + 1));
+    std::snprintf(buf, sizeof buf, "%s/sm%d/items2^%d/bytes2^%d/u16_%d/write_%d", name.c_str(),
+                  prop.multiProcessorCount, items_b, bytes_b,
+                  (int)(10.0 * u16 / c->batch_items + 0.5), (int)(10.0 * wr / c->batch_items + 0.5));
+    return std::string(buf);
+}
+
+bool tune_lookup(const char *path, const std::string &key, gbu::Tune *t)
+{
+    FILE *f = std::fopen(path, "r");
+    if (!f) return false;
+    char line[512], k[400];
+    int look = 0, ctas = 0;
+    bool found = false;
+    while (std::fgets(line, sizeof line, f)) {
+        if (line[0] == '#') continue;
+        if (std::sscanf(line, "%399s %d %d", k, &look, &ctas) == 3 && key == k) {
+            t->look = look;   // the last entry for a key wins
+            t->ctas_per_sm = ctas;
+            found = true;
+        }
+    }
+    std::fclose(f);
+    return found;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t gbu_batch_autotune(gbu_ctx *c, void *stream, const char *cache_path, gbu_tune *chosen)
+{
+    if (!c) return GBU_INVALID_ARG;
+    if (!ok(cudaSetDevice(c->device))) return GBU_DEVICE_ERROR;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    auto report = [&]() {
+        if (chosen) {
+            chosen->look_width = c->tune.look;
+            chosen->ctas_per_sm = c->tune.ctas_per_sm;
+        }
+        return GBU_OK;
+    };
+    if (c->batch_items == 0) return report();
+    const std::string key = tune_key(c);
+    if (key.empty()) return GBU_DEVICE_ERROR;
+    gbu::Tune cached;
+    if (cache_path && tune_lookup(cache_path, key, &cached)) {
+        gbu_tune t{cached.look, cached.ctas_per_sm};
+        if (gbu_set_tune(c, &t) == GBU_OK) return report();
+    }
+    const int per = job_max_ctas_per_sm(c->device);
+    if (per <= 0) return GBU_DEVICE_ERROR;
+    if (c->dirty && ensure_scratch(c, c->batch_chunks, s) != GBU_OK) return GBU_DEVICE_ERROR;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (!ok(cudaEventCreate(&e0)) || !ok(cudaEventCreate(&e1))) return GBU_DEVICE_ERROR;
+    gbu::Tune best = c->tune;
+    float best_ms = 1e30f;
+    int32_t st = GBU_OK;
+    constexpr int kReps = 3;
+    for (const int look : kLookWidths) {
+        for (int ctas = 1; ctas <= per && st == GBU_OK; ctas++) {
+            c->tune.look = look;
+            c->tune.ctas_per_sm = ctas;
+            st = batch_enqueue(c, s);   // warm-up
+            std::vector<float> ms;
+            for (int r = 0; r < kReps && st == GBU_OK; r++) {
+                float t = 0;
+                if (!ok(cudaEventRecord(e0, s)) || (st = batch_enqueue(c, s)) != GBU_OK ||
+                    !ok(cudaEventRecord(e1, s)) || !ok(cudaEventSynchronize(e1)) ||
+                    !ok(cudaEventElapsedTime(&t, e0, e1))) {
+                    if (st == GBU_OK) st = GBU_DEVICE_ERROR;
+                    break;
+                }
+                ms.push_back(t);
+            }
+            if (st != GBU_OK) break;
+            std::sort(ms.begin(), ms.end());
+            if (ms[kReps / 2] < best_ms) {
+                best_ms = ms[kReps / 2];
+                best = c->tune;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->tune = Tune{};
+    if (st != GBU_OK) return st;
+    gbu_tune t{best.look, best.ctas_per_sm};
+    st = gbu_set_tune(c, &t);
+    if (st != GBU_OK) return st;
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    if (cache_path) {
+        if (FILE *f = std::fopen(cache_path, "a")) {
+            std::fprintf(f, "%s %d %d %.4f\n", key.c_str(), best.look, best.ctas_per_sm, best_ms);
+            std::fclose(f);
+        }
+    }
+    return report();
 }
 
 const char *gbu_status_name(int32_t s)

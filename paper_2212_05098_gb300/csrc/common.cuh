@@ -87,7 +87,7 @@ struct ResultSlot {      // layout of gbu_result
 
 // One input of a job.
 enum : uint32_t { kOpUtf16 = 1u, kOpWrite = 2u };   // bit 0: input is UTF-16; bit 1: write output
-struct Item {
+struct __align__(16) Item {   // 64 bytes, copied into shared memory in 16-byte pieces
     const uint8_t *in_al;   // 16-byte aligned base at or before the input
     uint8_t *out;           // output (UTF-16 words or UTF-8 bytes)
     uint64_t n;             // input units
@@ -97,7 +97,9 @@ struct Item {
     uint32_t op;            // kOpUtf16 | kOpWrite
     uint32_t chunk_base;    // global index of the item's first chunk
     uint32_t nchunks;       // chunks of this item (at least 1)
+    uint32_t pad[2];
 };
+static_assert(sizeof(Item) == 64, "Item layout");
 
 // A job: one persistent launch over the chunks of one or more items.
 struct Job {
@@ -127,6 +129,16 @@ __device__ __forceinline__ uint64_t ld_relaxed(const unsigned long long *p)
 __device__ __forceinline__ void st_relaxed(unsigned long long *p, uint64_t v)
 {
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Add with acquire-release semantics at GPU scope: publishes this thread's
+// earlier writes with the increment and, for the thread that sees the final
+// count, makes every earlier incrementer's writes visible.
+__device__ __forceinline__ uint32_t atomic_add_acq_rel(unsigned int *p, uint32_t v)
+{
+    uint32_t old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
 }
 
 __device__ __forceinline__ uint64_t pack_status(uint64_t flag, uint32_t epoch, uint64_t value)
@@ -173,17 +185,14 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *w
 
 // Decoupled look-back, run by one full warp for the item chunk `k` (k > 0)
 // whose status words start at `status` (the item's first chunk). Each round
-// reads kLookWidth words per lane (the 32 * kLookWidth nearest predecessors
+// reads kLook words per lane (the 32 * kLook nearest predecessors
 // not yet summed) in one L2 round trip, sums aggregates back to the nearest
 // inclusive prefix, and moves on if there is none. Returns the chunk's
 // exclusive prefix (all lanes). On a wait longer than kSpinLimit polls, or as
 // soon as another CTA of the launch gave up, it sets the timeout flag and
 // returns what it has.
-#ifndef GBU_LOOK_WIDTH
-#define GBU_LOOK_WIDTH 8
-#endif
-constexpr int kLookWidth = GBU_LOOK_WIDTH;
-
+// kLook is a tuning parameter (see Tune in kernels.h).
+template <int kLook>
 __device__ __forceinline__ uint64_t lookback(const unsigned long long *status, uint32_t k,
                                              uint32_t epoch, unsigned int *flags)
 {
@@ -192,11 +201,11 @@ __device__ __forceinline__ uint64_t lookback(const unsigned long long *status, u
     int64_t base = (int64_t)k - 1;
     uint32_t rounds = 0;
     while (true) {
-        uint64_t val[kLookWidth];
-        uint32_t inc[kLookWidth], nr[kLookWidth];
+        uint64_t val[kLook];
+        uint32_t inc[kLook], nr[kLook];
         while (true) {
 #pragma unroll
-            for (int m = 0; m < kLookWidth; m++) {
+            for (int m = 0; m < kLook; m++) {
                 const int64_t idx = base - 32 * m - lane;
                 uint64_t flag = kFlagInclusive;   // before the item's first chunk: inclusive 0
                 val[m] = 0;
@@ -212,7 +221,7 @@ __device__ __forceinline__ uint64_t lookback(const unsigned long long *status, u
             // ready when no word before the nearest inclusive one is missing
             bool ready = true, found = false;
 #pragma unroll
-            for (int m = 0; m < kLookWidth; m++) {
+            for (int m = 0; m < kLook; m++) {
                 if (found) break;
                 const uint32_t upto = inc[m] ? ((inc[m] & (0u - inc[m])) - 1u) : 0xFFFFFFFFu;
                 if (nr[m] & upto) ready = false;
@@ -231,7 +240,7 @@ __device__ __forceinline__ uint64_t lookback(const unsigned long long *status, u
         uint64_t part = 0;
         bool found = false;
 #pragma unroll
-        for (int m = 0; m < kLookWidth; m++) {
+        for (int m = 0; m < kLook; m++) {
             if (found) break;
             if (inc[m]) {
                 const int l = __ffs(inc[m]) - 1;    // nearest predecessor with a full prefix
@@ -243,7 +252,7 @@ __device__ __forceinline__ uint64_t lookback(const unsigned long long *status, u
         }
         excl += warp_sum_u64(part);
         if (found) return excl;
-        base -= 32 * kLookWidth;
+        base -= 32 * kLook;
     }
 }
 
@@ -356,6 +365,18 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
         : "memory");
 }
 
+// Asynchronous 16-byte global -> shared copy (both addresses 16-byte
+// aligned), and the wait for all of this thread's outstanding copies.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(a), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 {
     uint32_t ok;
@@ -402,13 +423,25 @@ __device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t
 // One thread, after the item's last chunk was written: assemble the
 // gbu_result from the scan total and the first-error word, store it, and reset
 // the item's counters for the next launch.
+__device__ __forceinline__ void write_result(const Item &I, int32_t st, uint64_t off, uint64_t len)
+{
+    // No fence: results are read once the launch has completed.
+    volatile ResultSlot *r = I.result;
+    r->status = st;
+    r->reserved = 0;
+    r->in_offset = off;
+    r->out_len = len;
+}
+
+// Result of an item whose chunks are all counted (the caller's acquire made
+// every chunk's status, error key and error prefix visible); resets the
+// item's counters for the next launch.
 __device__ __forceinline__ void finalize_item(const Job &J, uint32_t it, const Item &I)
 {
-    __threadfence();
     const uint64_t total =
         ld_relaxed(&J.status[I.chunk_base + I.nchunks - 1]) & kValueMask;
     const uint64_t err = ld_relaxed(&J.item_err[it]);
-    const unsigned int flags = atomicAdd(J.flags, 0u);
+    const unsigned int flags = *reinterpret_cast<volatile unsigned int *>(J.flags);
     const uint32_t chunk_units = (I.op & kOpUtf16) ? kChunk16 : kChunk8;
     int32_t st;
     uint64_t off, len;
@@ -426,14 +459,25 @@ __device__ __forceinline__ void finalize_item(const Job &J, uint32_t it, const I
         off = I.n;
         len = total;
     }
-    volatile ResultSlot *r = I.result;
-    r->status = st;
-    r->reserved = 0;
-    r->in_offset = off;
-    r->out_len = len;
+    write_result(I, st, off, len);
     J.item_done[it] = 0;
     st_relaxed(&J.item_err[it], ~0ull);
-    __threadfence_system();
+}
+
+// Result of a one-chunk item straight from its chunk's aggregate and error
+// key (no shared counters involved).
+__device__ __forceinline__ void finalize_single(const Job &J, const Item &I, uint32_t agg,
+                                                uint64_t key)
+{
+    const unsigned int flags = *reinterpret_cast<volatile unsigned int *>(J.flags);
+    if (flags & 2u)
+        write_result(I, kDeviceError, 0, 0);
+    else if (flags & 1u)
+        write_result(I, kDeviceTimeout, 0, 0);
+    else if (key != ~0ull)
+        write_result(I, (int32_t)((key >> 15) & 0xFFu), key >> 23, key & 0x7FFFu);
+    else
+        write_result(I, ((I.op & kOpWrite) && agg > I.cap) ? kOutputTooSmall : kOk, I.n, agg);
 }
 
 }  // namespace gbu

@@ -25,11 +25,22 @@ constexpr size_t kHeaderBytes = 256;
 Item make_item(const void *in, uint64_t n, bool utf16, void *out, uint64_t cap, bool write,
                ResultSlot *result, uint32_t chunk_base);
 
-// Dynamic shared memory of one CTA; grid size that keeps every CTA resident.
+// Tuning parameters of a launch: look-back width (status words per lane per
+// round, one of kLookWidths) and resident CTAs per SM (0: as many as fit).
+constexpr int kLookWidths[] = {4, 8, 16};
+struct Tune {
+    int look = 8;
+    int ctas_per_sm = 0;
+};
+
+// Dynamic shared memory of one CTA; CTAs per SM that fit; grid size for a
+// tuning (every CTA resident); grid size with as many CTAs as fit.
 size_t job_smem_bytes(bool write);
+int job_max_ctas_per_sm(int device);
+int job_grid(int device, const Tune &t);
 int job_max_grid(int device);
 
-cudaError_t launch_job(const Job &J, bool write, int grid, cudaStream_t stream);
+cudaError_t launch_job(const Job &J, bool write, int grid, cudaStream_t stream, int look = 8);
 cudaError_t launch_write_result(ResultSlot *dst, int32_t status, uint64_t in_offset,
                                 uint64_t out_len, cudaStream_t stream);
 

@@ -169,7 +169,8 @@ struct St8 {
     uint32_t end[8];   // end-position indicators (bit 7 of each byte)
     uint32_t vmask;    // owned positions inside the input
     uint32_t bad;      // the fast check fired
-    bool edge, warp3, warp4;
+    bool skip;         // the whole warp lies outside the input (warp-uniform)
+    bool warp3, warp4;
 };
 
 // Load, classify, check structure, count units. Returns the thread's count.
@@ -184,9 +185,25 @@ __device__ __forceinline__ uint32_t chunk8_phase1(St8 &st, const uint8_t *stage,
     w[5] = b.x; w[6] = b.y; w[7] = b.z; w[8] = b.w;
     w[0] = *reinterpret_cast<const uint32_t *>(sp - 4);
     w[9] = *reinterpret_cast<const uint32_t *>(sp + 32);
+    // threads wholly outside the input (the tail of an item's last chunk)
+    // count nothing; a warp wholly outside skips the chunk body
+    const bool outside = vt + 32 <= lo || vt >= hi;
+    st.skip = __all_sync(kFull, outside);
+    st.bad = 0;
+    if (st.skip) {
+        st.vmask = 0;
+        st.warp3 = st.warp4 = false;
+        return 0;
+    }
     st.vmask = 0xFFFFFFFFu;
-    st.edge = vt < lo || vt + 32 > hi;
-    if (st.edge) {   // input edges only
+    bool masked = false;
+    if (outside) {
+#pragma unroll
+        for (int j = 0; j < 10; j++) w[j] = 0;
+        st.vmask = 0;
+        masked = true;
+    } else if (vt < lo || vt + 32 > hi) {   // straddles an end of the input
+        masked = true;
         st.vmask = 0;
 #pragma unroll
         for (int i = 0; i < 32; i++)
@@ -194,7 +211,7 @@ __device__ __forceinline__ uint32_t chunk8_phase1(St8 &st, const uint8_t *stage,
 #pragma unroll
         for (int j = 0; j < 8; j++) w[1 + j] = mask_word_bytes(w[1 + j], vt + 4 * j, lo, hi);
     }
-    if (vt - 4 < lo || vt + 36 > hi) {
+    if (!outside && (vt - 4 < lo || vt + 36 > hi)) {
         w[0] = mask_word_bytes(w[0], vt - 4, lo, hi);
         w[9] = mask_word_bytes(w[9], vt + 32, lo, hi);
     }
@@ -226,7 +243,7 @@ __device__ __forceinline__ uint32_t chunk8_phase1(St8 &st, const uint8_t *stage,
 #pragma unroll
         for (int j = 1; j <= 8; j++) {
             uint32_t e = (~ahead(ec[j - 1], ec[j], 8) | back(cl[j - 1].c4, cl[j].c4, 16)) & kB7;
-            if (st.edge) e &= spread4((st.vmask >> (4 * (j - 1))) & 0xFu);
+            if (masked) e &= spread4((st.vmask >> (4 * (j - 1))) & 0xFu);
             st.end[j - 1] = e;
             cnt += __popc(e);
         }
@@ -263,7 +280,11 @@ __device__ __forceinline__ void chunk8_phase2(St8 &st, const uint8_t *stage, uin
                                               uint32_t t_off, int64_t vt, int64_t lo, int64_t hi,
                                               unsigned long long *s_err)
 {
-    if (st.bad || st.edge) {
+    if (st.skip) return;
+    // Threads straddling an end of the input see the bytes outside it as
+    // zeros (ASCII), which neither create nor hide an error inside it, so
+    // the fast check covers them as well.
+    if (st.bad) {
         const uint64_t key = first_error_exact8(stage, vt, lo, hi, t_off);
         if (key != ~0ull) atomicMin(s_err, key);
     }
@@ -365,7 +386,9 @@ __device__ __forceinline__ uint32_t enc3(uint32_t u)
 struct St16 {
     uint32_t w[10];    // w[0]: words -2,-1; w[1..8]: own words 0..15; w[9]: words 16,17
     uint32_t vmask;
-    bool edge, general, only12;
+    bool edge;         // the thread's words straddle an end of the input
+    bool skip;         // the whole warp lies outside the input (warp-uniform)
+    bool general, only12;
 };
 
 __device__ __forceinline__ uint32_t unit_keep(int64_t u, int64_t lo, int64_t hi)
@@ -384,9 +407,25 @@ __device__ __forceinline__ uint32_t chunk16_phase1(St16 &st, const uint8_t *stag
     w[5] = b.x; w[6] = b.y; w[7] = b.z; w[8] = b.w;
     w[0] = *reinterpret_cast<const uint32_t *>(sp - 4);
     w[9] = *reinterpret_cast<const uint32_t *>(sp + 32);
+    // threads wholly outside the input count nothing; a warp wholly outside
+    // skips the chunk body
+    const bool outside = vt + 16 <= lo || vt >= hi;
+    st.skip = __all_sync(kFull, outside);
+    st.edge = false;
+    if (st.skip) {
+        st.vmask = 0;
+        st.general = st.only12 = false;
+        return 0;
+    }
     st.vmask = 0xFFFFu;
-    st.edge = vt < lo || vt + 16 > hi;
-    if (st.edge) {
+    bool masked = false;
+    if (outside) {
+#pragma unroll
+        for (int j = 0; j < 10; j++) w[j] = 0;
+        st.vmask = 0;
+        masked = true;
+    } else if (vt < lo || vt + 16 > hi) {   // straddles an end of the input
+        st.edge = masked = true;
         st.vmask = 0;
 #pragma unroll
         for (int i = 0; i < 16; i++)
@@ -395,7 +434,7 @@ __device__ __forceinline__ uint32_t chunk16_phase1(St16 &st, const uint8_t *stag
         for (int j = 0; j < 8; j++)
             w[1 + j] &= unit_keep(vt + 2 * j, lo, hi) | (unit_keep(vt + 2 * j + 1, lo, hi) << 16);
     }
-    if (vt - 2 < lo || vt + 18 > hi) {
+    if (!outside && (vt - 2 < lo || vt + 18 > hi)) {
         w[0] &= unit_keep(vt - 2, lo, hi) | (unit_keep(vt - 1, lo, hi) << 16);
         w[9] &= unit_keep(vt + 16, lo, hi) | (unit_keep(vt + 17, lo, hi) << 16);
     }
@@ -406,7 +445,7 @@ __device__ __forceinline__ uint32_t chunk16_phase1(St16 &st, const uint8_t *stag
         const uint32_t ga = ge80_lanes(x), gb = ge800_lanes(x), s = surr_lanes(x);
         const uint32_t lo_bit = (x << 5) & 0x80008000u;   // bit 10: low surrogate
         uint32_t vm = 0x80008000u;
-        if (st.edge)
+        if (masked)
             vm = (((st.vmask >> (2 * j)) & 1u) << 15) | (((st.vmask >> (2 * j + 1)) & 1u) << 31);
         // 1 + [>=80] + [>=800] + [high] - 3 [low]
         cnt += __popc(vm) + __popc(ga & vm) + __popc(gb & vm) + __popc(s & ~lo_bit & vm) -
@@ -423,6 +462,7 @@ template <bool kWrite>
 __device__ __forceinline__ void chunk16_phase2(const St16 &st, uint8_t *obuf, uint32_t t_off,
                                                int64_t vt, int64_t lo, unsigned long long *s_err)
 {
+    if (st.skip) return;
     const uint32_t *w = st.w;
     if (!st.general) {
         // no surrogates in this warp: every word is valid
@@ -497,18 +537,23 @@ struct Ring {
     uint32_t chunk[kStages], itidx[kStages], end[kStages];
 };
 
-// Thread 0: start the TMA load of chunk c (claimed earlier) into `slot`.
+// Thread 0: start the TMA load of chunk c (claimed earlier) into `slot`; `it`
+// is its item index and, in a batch, R.item[slot] its descriptor, both
+// fetched earlier (the descriptor by cp.async, waited for here).
 // Returns false (and marks the slot as the end) when the job is exhausted.
-__device__ __forceinline__ bool produce(const Job &J, uint32_t c, int slot, uint8_t *stages, Ring &R)
+__device__ __forceinline__ bool produce(const Job &J, uint32_t c, uint32_t it, int slot,
+                                        uint8_t *stages, Ring &R)
 {
     if (c >= J.total_chunks) {
         R.end[slot] = 1;
         mbar_arrive(&R.full[slot]);
         return false;
     }
-    const uint32_t it = J.chunk_item ? J.chunk_item[c] : 0u;
-    const Item I = J.items ? J.items[it] : J.item0;
-    R.item[slot] = I;
+    if (J.items)
+        cp_async_wait_all();
+    else
+        R.item[slot] = J.item0;
+    const Item I = R.item[slot];
     R.chunk[slot] = c;
     R.itidx[slot] = it;
     R.end[slot] = 0;
@@ -537,7 +582,7 @@ struct Pending {                 // a processed chunk waiting for its offset
 
 struct Done {                    // what the look-back warp keeps of a chunk until it is written
     uint64_t excl;
-    uint32_t chunk, itidx, nchunks;
+    uint32_t chunk, itidx, nchunks, agg;
 };
 
 // The last CTA out checks that every chunk id was handed out exactly once,
@@ -586,7 +631,7 @@ __device__ __forceinline__ void exit_job(const Job &J, uint32_t epoch)
 // Hand-over slots and their barriers come in fours (chunk j uses j&3): the
 // compute warps may hand over chunk j+2 before the look-back warp took
 // chunk j.
-template <bool kWrite>
+template <bool kWrite, int kLook>
 __global__ void __launch_bounds__(kBlock, kMinBlocks)
 transcode_kernel(const Job J)
 {
@@ -625,13 +670,16 @@ transcode_kernel(const Job J)
             if (!mbar_wait(&written_bar[j & 3], (j >> 2) & 1u)) return false;
             if (lead) {
                 const uint64_t key = s_errsnap[j & 3];
-                if (key != ~0ull) {
-                    J.err_prefix[d.chunk] = d.excl + (key & 0x7FFFu);
-                    atomicMin(&J.item_err[d.itidx], ((key >> 23) << 8) | ((key >> 15) & 0xFFu));
+                if (d.nchunks == 1) {
+                    finalize_single(J, J.items ? J.items[d.itidx] : J.item0, d.agg, key);
+                } else {
+                    if (key != ~0ull) {
+                        J.err_prefix[d.chunk] = d.excl + (key & 0x7FFFu);
+                        atomicMin(&J.item_err[d.itidx], ((key >> 23) << 8) | ((key >> 15) & 0xFFu));
+                    }
+                    if (atomic_add_acq_rel(&J.item_done[d.itidx], 1u) == d.nchunks - 1)
+                        finalize_item(J, d.itidx, J.items ? J.items[d.itidx] : J.item0);
                 }
-                __threadfence();
-                if (atomicAdd(&J.item_done[d.itidx], 1u) == d.nchunks - 1)
-                    finalize_item(J, d.itidx, J.items ? J.items[d.itidx] : J.item0);
             }
             return true;
         };
@@ -647,7 +695,7 @@ transcode_kernel(const Job J)
             const uint32_t k = P.chunk - P.item.chunk_base;
             uint64_t excl = 0;
             if (k > 0) {
-                excl = lookback(J.status + P.item.chunk_base, k, epoch, J.flags);
+                excl = lookback<kLook>(J.status + P.item.chunk_base, k, epoch, J.flags);
                 if (lead)
                     st_relaxed(&J.status[P.chunk], pack_status(kFlagInclusive, epoch, excl + P.agg));
             }
@@ -656,6 +704,7 @@ transcode_kernel(const Job J)
             d0.chunk = P.chunk;
             d0.itidx = P.itidx;
             d0.nchunks = P.item.nchunks;
+            d0.agg = P.agg;
             __syncwarp();
             if (lead) {
                 s_excl[q] = excl;
@@ -706,12 +755,36 @@ transcode_kernel(const Job J)
         return true;
     };
 
+    // Thread 0 feeds the ring. The chunk it loads at the top of iteration i
+    // was claimed at the top of iteration i-1, its item index fetched in the
+    // middle and its item descriptor at the end of iteration i-1, so none of
+    // these global round trips stalls the CTA.
     bool producing = true;   // meaningful in thread 0 only
-    uint32_t next_claim = 0;
+    uint32_t next_claim = 0, next_it = 0;
+    auto fetch_it = [&]() {
+        if (J.chunk_item && next_claim < J.total_chunks) next_it = J.chunk_item[next_claim];
+    };
+    // the descriptor goes straight into the ring slot of the next load
+    auto fetch_item = [&](int slot) {
+        if (J.items && next_claim < J.total_chunks) {
+            const uint8_t *src = reinterpret_cast<const uint8_t *>(J.items + next_it);
+            uint8_t *dst = reinterpret_cast<uint8_t *>(&R.item[slot]);
+#pragma unroll
+            for (int q = 0; q < (int)sizeof(Item); q += 16) cp_async16(dst + q, src + q);
+        }
+    };
     if (tid == 0) {
-        for (int s = 0; s < kStages - 1 && producing; s++)
-            producing = produce(J, atomicAdd(J.claim, 1u), s, stages, R);
-        if (producing) next_claim = atomicAdd(J.claim, 1u);
+        for (int s = 0; s < kStages - 1 && producing; s++) {
+            next_claim = atomicAdd(J.claim, 1u);
+            fetch_it();
+            fetch_item(s);
+            producing = produce(J, next_claim, next_it, s, stages, R);
+        }
+        if (producing) {   // the chunk loaded at the top of iteration 0
+            next_claim = atomicAdd(J.claim, 1u);
+            fetch_it();
+            fetch_item(kStages - 1);
+        }
     }
 
     uint32_t iter = 0, handed = 0;
@@ -720,7 +793,7 @@ transcode_kernel(const Job J)
         const int slot = iter % kStages;
         const int p = iter & 1;
         if (tid == 0 && producing) {
-            producing = produce(J, next_claim, (iter + kStages - 1) % kStages, stages, R);
+            producing = produce(J, next_claim, next_it, (iter + kStages - 1) % kStages, stages, R);
             if (producing) next_claim = atomicAdd(J.claim, 1u);   // used next iteration
         }
         const bool ok = mbar_wait(&R.full[slot], (iter / kStages) & 1u);
@@ -747,6 +820,7 @@ transcode_kernel(const Job J)
                 P.agg = agg;
                 P.end = 0;
                 mbar_arrive(&pend_bar[iter & 3]);
+                if (producing) fetch_it();
             }
             handed++;
         };
@@ -773,6 +847,9 @@ transcode_kernel(const Job J)
             }
             chunk8_phase2<kWrite>(st, stage, obuf, t_off, vt, lo, hi, &s_err[p]);
         }
+        // every thread read this iteration's R.item[slot] at its start: the
+        // slot's descriptor can be replaced by the one the next load needs
+        if (tid == 0 && producing) fetch_item(slot);
         cw_sync();
         iter++;
     }
@@ -787,7 +864,8 @@ transcode_kernel(const Job J)
     }
 }
 
-int g_max_grid[64] = {0};
+int g_max_per_sm[64] = {0};
+int g_sms[64] = {0};
 
 }  // namespace
 
@@ -796,34 +874,61 @@ size_t job_smem_bytes(bool write)
     return (size_t)kStages * kStageBytes + (write ? 2 * (size_t)kOutBufBytes : 0);
 }
 
-int job_max_grid(int device)
+// Every instantiation of the kernel: (write, look-back width).
+template <bool W, int L>
+constexpr const void *kernel_fn()
+{
+    return reinterpret_cast<const void *>(&transcode_kernel<W, L>);
+}
+
+const void *kernel_for(bool write, int look)
+{
+    switch (look) {
+    case 4: return write ? kernel_fn<true, 4>() : kernel_fn<false, 4>();
+    case 16: return write ? kernel_fn<true, 16>() : kernel_fn<false, 16>();
+    default: return write ? kernel_fn<true, 8>() : kernel_fn<false, 8>();
+    }
+}
+
+int job_max_ctas_per_sm(int device)
 {
     if (device < 0 || device >= 64) return 0;
-    if (g_max_grid[device]) return g_max_grid[device];
+    if (g_max_per_sm[device]) return g_max_per_sm[device];
     int sms = 0, per = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
         return 0;
-    for (int w = 0; w < 2; w++) {
-        const void *fn = w ? (const void *)transcode_kernel<true> : (const void *)transcode_kernel<false>;
-        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)job_smem_bytes(w != 0)) != cudaSuccess)
-            return 0;
-    }
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, transcode_kernel<true>, kBlock,
+    for (const int look : kLookWidths)
+        for (int w = 0; w < 2; w++)
+            if (cudaFuncSetAttribute(kernel_for(w != 0, look), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)job_smem_bytes(w != 0)) != cudaSuccess)
+                return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel_for(true, 8), kBlock,
                                                       job_smem_bytes(true)) != cudaSuccess ||
         per < 1)
         per = 1;
-    g_max_grid[device] = sms * per;
-    return g_max_grid[device];
+    g_sms[device] = sms;
+    g_max_per_sm[device] = per;
+    return per;
 }
 
-cudaError_t launch_job(const Job &J, bool write, int grid, cudaStream_t stream)
+int job_grid(int device, const Tune &t)
 {
-    if (write)
-        transcode_kernel<true><<<grid, kBlock, job_smem_bytes(true), stream>>>(J);
-    else
-        transcode_kernel<false><<<grid, kBlock, job_smem_bytes(false), stream>>>(J);
-    return cudaGetLastError();
+    const int per = job_max_ctas_per_sm(device);
+    if (per <= 0) return 0;
+    const int use = t.ctas_per_sm > 0 && t.ctas_per_sm < per ? t.ctas_per_sm : per;
+    return g_sms[device] * use;
+}
+
+int job_max_grid(int device)
+{
+    return job_grid(device, Tune{});
+}
+
+cudaError_t launch_job(const Job &J, bool write, int grid, cudaStream_t stream, int look)
+{
+    void *args[] = {const_cast<Job *>(&J)};
+    return cudaLaunchKernel(kernel_for(write, look), dim3(grid), dim3(kBlock), args,
+                            job_smem_bytes(write), stream);
 }
 
 __global__ void write_result_kernel(ResultSlot *dst, int32_t status, uint64_t in_offset,

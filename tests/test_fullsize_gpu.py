@@ -99,3 +99,79 @@ def test_validation_stress_1000_cases(env, enc):
                 ref = oracle.utf8_length_from_utf16le(patched)
             assert (r.status, r.in_offset, r.out_len) == (ref.status, ref.in_offset, ref.out_len)
         d_in[lo:hi] = torch.from_numpy(t.data[lo:hi]).cuda()   # undo the patch
+
+
+def test_batched_200k_strings(env):
+    """The batched workload at full size: 200,000 strings, lengths log-uniform
+    16 B - 1 MiB (about 18 GiB), windows of 256 MiB corpora of the four
+    profiles in both encodings, one autotuned graph-captured launch. Every
+    result is checked against properties of valid text (status OK, whole
+    input consumed, output length from the characters' encoded sizes) and
+    300 sampled strings against the oracle byte for byte."""
+    torch, pool, ctx = env
+    from textgen import batch as tbatch
+    corpora, d_corp = [], []
+    for p in textgen.BENCH_PROFILES:
+        for enc in (textgen.UTF8, textgen.UTF16):
+            t = textgen.generate(p, 256 << 20, enc, executor=pool, keep_cps=False, keep_lens=False)
+            corpora.append((p, enc, t.data))
+            d_corp.append(torch.from_numpy(t.data).cuda())
+    lay = tbatch.layout(corpora, 200_000, 16, 1 << 20, seed=4)
+    n = lay.nbytes.size
+    is16 = np.array([corpora[k][1] == textgen.UTF16 for k in lay.corpus])
+    cap_b = np.where(is16, 3 * (lay.nbytes // 2), 2 * lay.nbytes)
+    off = np.zeros(n + 1, np.int64)
+    np.cumsum((cap_b + 15) // 16 * 16, out=off[1:])
+    d_out = torch.empty(int(off[-1]) + 16, dtype=torch.uint8, device="cuda")
+    d_res = torch.zeros(n * 24, dtype=torch.uint8, device="cuda")
+    items = []
+    for i in range(n):
+        k = int(lay.corpus[i])
+        inp = d_corp[k].data_ptr() + int(lay.start[i])
+        u = int(lay.nbytes[i]) // (2 if is16[i] else 1)
+        items.append((inp if u else 0, u, d_out.data_ptr() + int(off[i]),
+                      3 * u if is16[i] else u,
+                      gbu.GBU_OP_UTF16LE_TO_UTF8 if is16[i] else gbu.GBU_OP_UTF8_TO_UTF16LE))
+    assert gbu.gbu_batch_plan(ctx, items, d_res.data_ptr(), 0) == gbu.GBU_OK
+    st, _ = gbu.gbu_batch_autotune(ctx, 0, None)
+    try:
+        assert st == gbu.GBU_OK
+        d_out.fill_(0xA5)
+        assert gbu.gbu_batch_launch_graph(ctx, 0) == gbu.GBU_OK
+        torch.cuda.synchronize()
+        res = np.frombuffer(d_res.cpu().numpy().tobytes(),
+                            dtype=[("status", "<i4"), ("r", "<u4"), ("off", "<u8"), ("len", "<u8")])
+        assert (res["status"] == 0).all()
+        assert (res["off"] == lay.nbytes // np.where(is16, 2, 1)).all()
+        # output length of valid text: UTF-8 -> UTF-16 units = non-continuation
+        # bytes + 4-byte leads; UTF-16 -> UTF-8 bytes = per-unit sizes, 2 per
+        # surrogate (4 per pair)
+        for k, (p, enc, data) in enumerate(corpora):
+            sel = np.nonzero(lay.corpus == k)[0]
+            if enc == textgen.UTF8:
+                w = (((data & 0xC0) != 0x80).astype(np.int64) + (data >= 0xF0))
+            else:
+                u = data.view("<u2")
+                w = np.where(u < 0x80, 1, np.where(u < 0x800, 2, np.where((u & 0xF800) == 0xD800, 2, 3)))
+                w = w.astype(np.int64)
+            cum = np.zeros(w.size + 1, np.int64)
+            np.cumsum(w, out=cum[1:])
+            ub = 2 if enc == textgen.UTF16 else 1
+            s0, s1 = lay.start[sel] // ub, (lay.start[sel] + lay.nbytes[sel]) // ub
+            assert (res["len"][sel] == cum[s1] - cum[s0]).all(), (p, enc)
+        rng = np.random.default_rng(86)
+        for i in rng.choice(n, 300, replace=False):
+            k = int(lay.corpus[i])
+            src = corpora[k][2][int(lay.start[i]):int(lay.start[i] + lay.nbytes[i])]
+            if is16[i]:
+                ref, ref_out = oracle.utf16le_to_utf8(src)
+                want = ref_out
+            else:
+                ref, ref_out = oracle.utf8_to_utf16le(src)
+                want = ref_out.view(np.uint8)
+            assert (int(res["status"][i]), int(res["off"][i]), int(res["len"][i])) == \
+                (ref.status, ref.in_offset, ref.out_len)
+            got = d_out[int(off[i]):int(off[i]) + want.size].cpu().numpy()
+            assert np.array_equal(got, want), i
+    finally:
+        assert gbu.gbu_set_tune(ctx, 8, 0) == gbu.GBU_OK

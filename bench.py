@@ -63,10 +63,17 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=256 << 20,
                     help="bytes of each buffer the oracle baseline transcodes")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["single", "batched"], default="single",
+    ap.add_argument("--workload", choices=["single", "batched", "serving"], default="single",
                     help="single: 4 profiles x 2 directions x one buffer each (default); "
-                         "batched: many strings in one persistent graph-captured launch")
+                         "batched: many strings in one persistent graph-captured launch; "
+                         "serving: Poisson request arrivals through the serving loop")
     ap.add_argument("--strings", type=int, default=200_000, help="batched: number of strings")
+    ap.add_argument("--rates", default="0.1,0.25,0.5,0.75,0.9,1.0,1.2",
+                    help="serving: arrival rates as fractions of the plain kernel's GB/s")
+    ap.add_argument("--serve-seconds", type=float, default=0.5,
+                    help="serving: arrival window per rate (seconds)")
+    ap.add_argument("--pool-gib", type=float, default=8.0, help="serving: device pool (GiB)")
+    ap.add_argument("--slots", type=int, default=2, help="serving: batches in flight")
     ap.add_argument("--batch-total", type=int, default=0,
                     help="batched: scale the string lengths so that they add up to this many "
                          "bytes (0: unscaled, log-uniform 16 B - 1 MiB)")
@@ -245,6 +252,9 @@ def main():
         return
     if args.workload == "batched":
         run_batched(args, rank, world, local)
+        return
+    if args.workload == "serving":
+        run_serving(args, rank, world, local)
         return
     # process pool for the generator: started before the first CUDA call
     pool = textgen.process_pool() if args.size >= (64 << 20) else None
@@ -644,6 +654,153 @@ def run_batched(args, rank, world, local):
         print(json.dumps(line), flush=True)
     plain.close()
     ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+SERVE_METRIC = ("sustained input GB/s and p50/p99 request latency, validated UTF-8<->UTF-16LE "
+                "transcoding through the serving loop (continuous batching)")
+
+
+def run_serving(args, rank, world, local):
+    """Serving workload: requests of log-uniform size over 64 B - 16 MiB
+    (windows of the per-profile corpora, profile uniform, direction 50/50),
+    1 % with one injected error, arriving as a Poisson process, replayed in
+    real time through the library's serving loop (dispatcher thread,
+    continuous batching, admission by bytes against a device pool). For each
+    arrival rate (a fraction of the plain kernel's GB/s measured in the same
+    run) it reports the sustained input GB/s and the p50/p99 latency from
+    arrival to completion."""
+    from textgen import batch as tbatch
+    pool = textgen.process_pool()
+    import torch
+    import torch.distributed as dist
+
+    import paper_2212_05098_gb300 as gbu
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    profiles = args.profiles.split(",")
+    cases = gen_inputs(profiles, args.size, rank, pool)
+    pool.shutdown()
+    corpora = [(c["profile"], textgen.UTF8 if c["dir"] == "utf8_to_utf16le" else textgen.UTF16,
+                c["data"]) for c in cases]
+    gbu.load()
+    d_corp = [torch.from_numpy(c["data"]).cuda() for c in cases]
+
+    # the plain single-buffer kernel on the corpora: the reference rate
+    plain = gbu.Context(local)
+    plain.reserve(args.size)
+    scratch_out = torch.empty(2 * args.size + 64, dtype=torch.uint8, device="cuda")
+    res1 = torch.zeros(4, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.Stream()
+    sh = stream.cuda_stream
+
+    def single():
+        for c, d in zip(cases, d_corp):
+            if c["dir"] == "utf8_to_utf16le":
+                gbu.gbu_utf8_to_utf16le_async(plain.handle, d.data_ptr(), d.numel(),
+                                              scratch_out.data_ptr(), d.numel(), res1.data_ptr(), sh)
+            else:
+                gbu.gbu_utf16le_to_utf8_async(plain.handle, d.data_ptr(), d.numel() // 2,
+                                              scratch_out.data_ptr(), 3 * (d.numel() // 2),
+                                              res1.data_ptr(), sh)
+
+    single()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(3):
+        single()
+    e1.record(stream)
+    stream.synchronize()
+    plain_gbs = 3 * sum(d.numel() for d in d_corp) / (e0.elapsed_time(e1) / 1e3) / 1e9
+    plain.close()
+    del scratch_out
+
+    srv = gbu.gbu_server_create(local, int(args.pool_gib * (1 << 30)), args.slots, 4096)
+    if not srv:
+        raise RuntimeError("server creation failed")
+    mean_bytes = (16 << 20) - 64
+    mean_bytes /= np.log((16 << 20) / 64)
+    sweep = []
+    sampler = ClockSampler(local)
+    t_wall0 = time.time()
+    launches0 = gbu.gbu_kernel_launch_count()
+    for ri, frac in enumerate(float(x) for x in args.rates.split(",")):
+        rate = frac * plain_gbs * 1e9 / mean_bytes          # requests per second
+        n_req = int(min(200_000, max(2000, rate * args.serve_seconds)))
+        tr = tbatch.serving_trace(corpora, n_req, rate, seed=5 + 1000 * rank + ri)
+        lay = tr.layout
+        keep, reqs = [], []
+        for i in range(n_req):
+            k = int(lay.corpus[i])
+            enc = corpora[k][1]
+            s0, nb = int(lay.start[i]), int(lay.nbytes[i])
+            if tr.error_at[i] >= 0:
+                host = tbatch.inject_error(corpora[k][2][s0:s0 + nb], int(tr.error_at[i]), enc)
+                dev = torch.from_numpy(host).cuda()
+                keep.append(dev)
+                ptr = dev.data_ptr()
+            else:
+                ptr = d_corp[k].data_ptr() + s0
+            u16 = enc == textgen.UTF16
+            op = gbu.GBU_OP_UTF16LE_TO_UTF8 if u16 else gbu.GBU_OP_UTF8_TO_UTF16LE
+            reqs.append((op, ptr if nb else 0, nb // 2 if u16 else nb, 0, 0, i))
+        torch.cuda.synchronize()
+        st, comp = gbu.gbu_server_replay(srv, reqs, list(tr.t_arrival), 300.0)
+        if st != gbu.GBU_OK:
+            raise RuntimeError(f"replay: {gbu.status_name(st)}")
+        # latency from the scheduled arrival (the replay's clock starts at 0)
+        lat = np.array([comp[i].t_done - tr.t_arrival[i] for i in range(n_req)])
+        lag = np.array([comp[i].t_submit - tr.t_arrival[i] for i in range(n_req)])
+        t_first = float(tr.t_arrival[0])
+        t_last = max(comp[i].t_done for i in range(n_req))
+        status = np.array([comp[i].result.status for i in range(n_req)])
+        n_err = int((tr.error_at >= 0).sum())
+        if (status != 0).sum() != n_err or (status[tr.error_at >= 0] == 0).any():
+            raise RuntimeError("unexpected request status in the serving run")
+        items = np.array([comp[i].batch_items for i in range(n_req)])
+        sweep.append({
+            "load_frac": frac, "rate_req_s": rate, "requests": n_req,
+            "input_bytes": lay.total_bytes, "errors": n_err,
+            "sustained_gbs": lay.total_bytes / (t_last - t_first) / 1e9,
+            "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "mean_ms": float(lat.mean() * 1e3),
+            "mean_batch_items": float(items.mean()),
+            "max_submit_lag_ms": float(lag.max() * 1e3),
+            "batches": len({comp[i].batch for i in range(n_req)}),
+        })
+        del keep
+    t_wall1 = time.time()
+    launches = gbu.gbu_kernel_launch_count() - launches0
+    sampler.stop()
+    clocks = sampler.summary(t_wall0, t_wall1)
+    stats = gbu.gbu_server_stats(srv)
+    gbu.gbu_server_destroy(srv)
+    top = max(sweep, key=lambda x: x["sustained_gbs"])
+    if rank == 0:
+        line = {
+            "metric": SERVE_METRIC, "value": top["sustained_gbs"], "unit": "GB/s",
+            "n_gpus": world, "steps": len(sweep), "warmup": 0,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8+u16",
+            "data": "synthetic (windows of seeded per-profile corpora, 1 % injected errors)",
+            "config": {"workload": "Poisson arrivals, sizes log-uniform 64 B-16 MiB, profiles "
+                                   "uniform over 4, direction 50/50, 1 % injected errors",
+                       "pool_bytes": stats.pool_bytes, "pool_high_water": stats.pool_high_water,
+                       "slots": args.slots, "max_batch_items": 4096,
+                       "rates": "fractions of the plain kernel's GB/s in this run",
+                       "latency": "scheduled arrival to completion observed by the dispatcher"},
+            "p50_ms_at_best": top["p50_ms"], "p99_ms_at_best": top["p99_ms"],
+            "sweep": sweep,
+            "plain_single_buffer_gbs": plain_gbs,
+            "plain_over_served": plain_gbs / top["sustained_gbs"],
+            "cpu_baseline": None, "e2e": None, "clocks": clocks,
+            "gpu_launches": launches,
+        }
+        print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
 

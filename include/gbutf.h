@@ -211,6 +211,74 @@ int32_t gbu_set_tune(gbu_ctx *ctx, const gbu_tune *tune);
  * GBU_INVALID_ARG or GBU_DEVICE_ERROR (a failing launch). */
 int32_t gbu_batch_autotune(gbu_ctx *ctx, void *stream, const char *cache_path, gbu_tune *chosen);
 
+/* ---- Serving: requests as they arrive, continuous batching ------------------
+ *
+ * Not a construct of the paper (which transcodes one buffer per call): a
+ * server that takes transcode requests of any size and direction as they
+ * arrive. A dispatcher thread keeps up to `slots` batches in flight on the
+ * GPU, each on its own stream and context. Whenever a slot is free it admits
+ * queued requests in arrival order while their bytes fit into a device memory
+ * pool of `pool_bytes` (each request holds a block for a copy of its input and
+ * its worst-case output until it completes), copies their inputs into the
+ * pool and runs them as one batch (see gbu_batch_plan). Requests that arrive
+ * while batches run are admitted as soon as a slot and pool space free up, so
+ * their work overlaps with the batches in flight. Each request's result is
+ * that of the single-buffer call on the same input (gbu_result semantics).
+ * The library owns the pool, streams and thread; the caller owns request
+ * inputs (device memory, read during the request's batch) and the optional
+ * output destinations. */
+typedef struct gbu_server gbu_server;
+
+typedef struct gbu_request {
+    int32_t op;                   /* gbu_op                                                    */
+    uint32_t reserved;            /* zero                                                      */
+    const void *in;               /* device pointer: UTF-8 bytes or UTF-16LE words (2-aligned) */
+    uint64_t n;                   /* input units                                               */
+    void *out_copy;               /* device pointer receiving the output, or NULL (discarded)  */
+    uint64_t out_copy_cap_bytes;  /* bytes available at out_copy (the worst-case output,
+                                     2n for UTF-8 -> UTF-16LE and 3n for UTF-16LE -> UTF-8,
+                                     is copied when it fits; bytes past out_len unspecified)  */
+    uint64_t tag;                 /* caller's identifier, returned in the completion           */
+} gbu_request;
+
+typedef struct gbu_completion {
+    uint64_t tag;
+    gbu_result result;
+    double t_submit, t_admit, t_launch, t_done;   /* seconds (server clock, or replay start) */
+    uint32_t batch;                               /* batch number                             */
+    uint32_t batch_items;                         /* requests in that batch                   */
+} gbu_completion;
+
+typedef struct gbu_server_stats_t {
+    uint64_t submitted, completed, batches, pool_bytes, pool_high_water;
+} gbu_server_stats_t;
+
+/* Create a server on `device`: a pool of pool_bytes (>= 1 MiB), 1..16 slots,
+ * at most max_batch_items requests per batch. NULL on failure. */
+gbu_server *gbu_server_create(int device, uint64_t pool_bytes, uint32_t slots,
+                              uint32_t max_batch_items);
+/* Stop the dispatcher (queued requests are dropped) and free everything. */
+void gbu_server_destroy(gbu_server *srv);
+/* Queue one request (copied). GBU_INVALID_ARG: bad op, null or misaligned
+ * input, or a request whose block can never fit into the pool. */
+int32_t gbu_server_submit(gbu_server *srv, const gbu_request *req);
+/* Move up to `max` completions (in completion order) into `out`; returns how
+ * many. */
+uint32_t gbu_server_poll(gbu_server *srv, gbu_completion *out, uint32_t max);
+/* Wait until every submitted request has completed (GBU_DEVICE_TIMEOUT after
+ * timeout_s seconds). */
+int32_t gbu_server_wait_idle(gbu_server *srv, double timeout_s);
+/* Submit reqs[i] at t_arrival[i] seconds after the call (non-decreasing
+ * times, from this thread), collect every completion and return them in
+ * request order in out[i] (times relative to the call). Must not be mixed
+ * with concurrent gbu_server_submit / gbu_server_poll calls. Returns GBU_OK,
+ * GBU_INVALID_ARG (bad request; nothing submitted) or GBU_DEVICE_TIMEOUT (not
+ * all completed within timeout_s after the last arrival). */
+int32_t gbu_server_replay(gbu_server *srv, const gbu_request *reqs, const double *t_arrival,
+                          uint32_t count, gbu_completion *out, double timeout_s);
+/* Counters of the server. */
+int32_t gbu_server_stats(gbu_server *srv, gbu_server_stats_t *stats);
+
 /* No-allocation form of gbu_utf8_to_utf16le. The paper has no counterpart to
  * this call: it is for callers that may not allocate device memory (another
  * component owns the device's memory, or an allocation's implicit device

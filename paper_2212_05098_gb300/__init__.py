@@ -67,6 +67,25 @@ class gbu_tune(ctypes.Structure):
     _fields_ = [("look_width", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
 
 
+class gbu_request(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int32), ("reserved", ctypes.c_uint32), ("in_", ctypes.c_void_p),
+                ("n", ctypes.c_uint64), ("out_copy", ctypes.c_void_p),
+                ("out_copy_cap_bytes", ctypes.c_uint64), ("tag", ctypes.c_uint64)]
+
+
+class gbu_completion(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("result", gbu_result), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_launch", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("batch", ctypes.c_uint32),
+                ("batch_items", ctypes.c_uint32)]
+
+
+class gbu_server_stats_t(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("batches", ctypes.c_uint64), ("pool_bytes", ctypes.c_uint64),
+                ("pool_high_water", ctypes.c_uint64)]
+
+
 # name -> (restype, argtypes)
 _VP, _U64, _I32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int32
 _RP = ctypes.POINTER(gbu_result)
@@ -90,6 +109,14 @@ SIGNATURES = {
     "gbu_get_tune": (_I32, [_VP, ctypes.POINTER(gbu_tune)]),
     "gbu_set_tune": (_I32, [_VP, ctypes.POINTER(gbu_tune)]),
     "gbu_batch_autotune": (_I32, [_VP, _VP, ctypes.c_char_p, ctypes.POINTER(gbu_tune)]),
+    "gbu_server_create": (_VP, [ctypes.c_int, _U64, ctypes.c_uint32, ctypes.c_uint32]),
+    "gbu_server_destroy": (None, [_VP]),
+    "gbu_server_submit": (_I32, [_VP, ctypes.POINTER(gbu_request)]),
+    "gbu_server_poll": (ctypes.c_uint32, [_VP, ctypes.POINTER(gbu_completion), ctypes.c_uint32]),
+    "gbu_server_wait_idle": (_I32, [_VP, ctypes.c_double]),
+    "gbu_server_replay": (_I32, [_VP, ctypes.POINTER(gbu_request), ctypes.POINTER(ctypes.c_double),
+                                 ctypes.c_uint32, ctypes.POINTER(gbu_completion), ctypes.c_double]),
+    "gbu_server_stats": (_I32, [_VP, ctypes.POINTER(gbu_server_stats_t)]),
     "gbu_utf8_to_utf16le_noalloc": (gbu_result, [_VP, _U64, _VP, _U64, _VP]),
     "gbu_status_name": (ctypes.c_char_p, [_I32]),
     "gbu_kernel_launch_count": (_U64, []),
@@ -214,6 +241,49 @@ def gbu_batch_autotune(ctx, stream=0, cache_path: str | None = None):
     path = cache_path.encode() if cache_path else None
     st = load().gbu_batch_autotune(ctx, stream, path, ctypes.byref(t))
     return st, t
+
+
+def gbu_server_create(device: int, pool_bytes: int, slots: int, max_batch_items: int) -> int:
+    return load().gbu_server_create(device, pool_bytes, slots, max_batch_items)
+
+
+def gbu_server_destroy(srv) -> None:
+    load().gbu_server_destroy(srv)
+
+
+def gbu_server_submit(srv, op: int, in_ptr: int, n: int, out_copy: int = 0,
+                      out_copy_cap_bytes: int = 0, tag: int = 0) -> int:
+    r = gbu_request(op, 0, in_ptr or None, n, out_copy or None, out_copy_cap_bytes, tag)
+    return load().gbu_server_submit(srv, ctypes.byref(r))
+
+
+def gbu_server_poll(srv, max_items: int = 1024) -> list:
+    buf = (gbu_completion * max_items)()
+    k = load().gbu_server_poll(srv, buf, max_items)
+    return [buf[i] for i in range(k)]
+
+
+def gbu_server_wait_idle(srv, timeout_s: float = 60.0) -> int:
+    return load().gbu_server_wait_idle(srv, timeout_s)
+
+
+def gbu_server_replay(srv, requests, t_arrival, timeout_s: float = 120.0):
+    """requests: sequence of (op, in_ptr, n, out_copy, out_copy_cap_bytes, tag);
+    t_arrival: seconds after the call. Returns (status, completion array)."""
+    k = len(requests)
+    reqs = (gbu_request * max(1, k))()
+    for i, (op, inp, n, oc, occ, tag) in enumerate(requests):
+        reqs[i] = gbu_request(op, 0, inp or None, n, oc or None, occ, tag)
+    times = (ctypes.c_double * max(1, k))(*t_arrival)
+    out = (gbu_completion * max(1, k))()
+    st = load().gbu_server_replay(srv, reqs, times, k, out, timeout_s)
+    return st, out
+
+
+def gbu_server_stats(srv) -> gbu_server_stats_t:
+    st = gbu_server_stats_t()
+    load().gbu_server_stats(srv, ctypes.byref(st))
+    return st
 
 
 def gbu_utf8_to_utf16le_noalloc(d_in, n_bytes, d_out, cap_units, stream=0) -> Result:

@@ -79,3 +79,47 @@ def layout(corpora: list[tuple[str, str, np.ndarray]], n: int, lo: int, hi: int,
         t = np.maximum(t, s)
         start[sel], end[sel] = s, t
     return Layout(corpus, start, end - start)
+
+
+@dataclass
+class Trace:
+    layout: Layout
+    t_arrival: np.ndarray      # float64 seconds, non-decreasing
+    error_at: np.ndarray       # int64 byte offset of the injected error in the string, -1: none
+
+
+def poisson_arrivals(n: int, rate: float, seed: int) -> np.ndarray:
+    """n arrival times (seconds) of a Poisson process of `rate` per second."""
+    rng = _rng(seed, 1 << 43)
+    return np.cumsum(rng.exponential(1.0 / rate, size=n))
+
+
+def serving_trace(corpora, n: int, rate: float, seed: int, lo: int = 64, hi: int = 16 << 20,
+                  error_frac: float = 0.01) -> Trace:
+    """Requests of a serving run: sizes log-uniform over [lo, hi] bytes,
+    profile uniform, direction 50/50 (as `layout`), Poisson arrivals at `rate`
+    requests per second, and `error_frac` of them marked for one injected
+    error at a uniform position (see `inject_error`)."""
+    lay = layout(corpora, n, lo, hi, seed)
+    rng = _rng(seed, 1 << 44)
+    err = rng.random(n) < error_frac
+    pos = (rng.random(n) * np.maximum(lay.nbytes, 1)).astype(np.int64)
+    error_at = np.where(err & (lay.nbytes > 0), pos, -1)
+    return Trace(lay, poisson_arrivals(n, rate, seed), error_at)
+
+
+def inject_error(data: np.ndarray, at: int, encoding: str) -> np.ndarray:
+    """A copy of `data` (one string) with an invalid unit written at byte `at`:
+    0xFF in UTF-8 (a byte that never occurs in UTF-8), or a high surrogate
+    followed by U+0041 in UTF-16LE (a lone high surrogate). The first error of
+    the result is at or before that position."""
+    out = data.copy()
+    if encoding == UTF8:
+        out[at] = 0xFF
+    else:
+        w = out.view("<u2")
+        u = at // 2
+        w[u] = 0xD800
+        if u + 1 < w.size:
+            w[u + 1] = 0x0041
+    return out

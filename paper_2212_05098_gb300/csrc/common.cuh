@@ -45,7 +45,10 @@ constexpr uint32_t kChunkBytes = 8192;
 constexpr uint32_t kChunk8 = kChunkBytes;        // UTF-8 bytes per chunk
 constexpr uint32_t kChunk16 = kChunkBytes / 2;   // UTF-16 words per chunk
 // Input ring: each stage holds one chunk plus kHalo bytes on each side.
-constexpr int kStages = 3;
+#ifndef GBU_STAGES
+#define GBU_STAGES 2
+#endif
+constexpr int kStages = GBU_STAGES;
 constexpr uint32_t kHalo = 16;
 constexpr uint32_t kStageBytes = kChunkBytes + 2 * kHalo;
 // Output staging capacity per chunk. UTF-8 -> UTF-16: at most one unit per
@@ -153,8 +156,11 @@ __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v)
     return v;
 }
 
-// Exclusive scan of one uint32 per compute thread (kThreads threads).
-// Returns the thread's exclusive prefix; *total receives the block sum.
+// Exclusive scan of one uint32 per compute thread (kThreads threads), with
+// one barrier: every warp scans its lanes and posts its total; after the
+// barrier every thread adds up the totals of the warps before its own.
+// Returns the thread's exclusive prefix; *total receives the block sum. The
+// caller must not reuse warp_tot before another compute-thread barrier.
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *warp_tot,
                                                          uint32_t *total)
 {
@@ -162,25 +168,20 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *w
     uint32_t inc = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        uint32_t t = __shfl_up_sync(kFull, inc, o);
+        const uint32_t t = __shfl_up_sync(kFull, inc, o);
         if (lane >= o) inc += t;
     }
     if (lane == 31) warp_tot[warp] = inc;
     cw_sync();
-    if (warp == 0) {
-        uint32_t w = lane < kThreads / 32 ? warp_tot[lane] : 0;
-        uint32_t wi = w;
+    uint32_t base = 0, sum = 0;
 #pragma unroll
-        for (int o = 1; o < kThreads / 32; o <<= 1) {
-            uint32_t t = __shfl_up_sync(kFull, wi, o);
-            if (lane >= o) wi += t;
-        }
-        if (lane < kThreads / 32) warp_tot[lane] = wi - w;   // exclusive warp base
-        if (lane == kThreads / 32 - 1) warp_tot[kThreads / 32] = wi;
+    for (int w = 0; w < kThreads / 32; w++) {
+        const uint32_t t = warp_tot[w];
+        base += w < warp ? t : 0u;
+        sum += t;
     }
-    cw_sync();
-    *total = warp_tot[kThreads / 32];
-    return warp_tot[warp] + inc - v;
+    *total = sum;
+    return base + inc - v;
 }
 
 // Decoupled look-back, run by one full warp for the item chunk `k` (k > 0)

@@ -12,11 +12,11 @@
 //     chunk's aggregate for the decoupled look-back;
 //   * a ninth warp looks back for the chunk's offset as soon as its aggregate
 //     is out and publishes the inclusive prefix;
-//   * the compute threads assemble the chunk's output into one of two
-//     shared-memory staging buffers and write it out with 16-byte stores two
-//     iterations later, when its offset is long known.
+//   * the compute threads assemble the chunk's output into one of kDepth
+//     shared-memory staging buffers and write it out with 16-byte stores
+//     kDepth iterations later, when its offset is long known.
 // The compute warps thus practically never wait on a look-back, and the TMA
-// ring keeps two chunks of input in flight per CTA.
+// ring loads the next chunk while the current one is processed.
 //
 // Ownership: a UTF-8 unit belongs to the thread holding its end position
 // (see chunk8 below); a UTF-16 surrogate pair belongs to the owner of its
@@ -538,21 +538,23 @@ struct Ring {
 };
 
 // Thread 0: start the TMA load of chunk c (claimed earlier) into `slot`; `it`
-// is its item index and, in a batch, R.item[slot] its descriptor, both
-// fetched earlier (the descriptor by cp.async, waited for here).
+// is its item index and, in a batch, *pre its descriptor, both fetched
+// earlier (the descriptor by cp.async, waited for here).
 // Returns false (and marks the slot as the end) when the job is exhausted.
-__device__ __forceinline__ bool produce(const Job &J, uint32_t c, uint32_t it, int slot,
-                                        uint8_t *stages, Ring &R)
+__device__ __forceinline__ bool produce(const Job &J, uint32_t c, uint32_t it, const Item *pre,
+                                        int slot, uint8_t *stages, Ring &R)
 {
     if (c >= J.total_chunks) {
         R.end[slot] = 1;
         mbar_arrive(&R.full[slot]);
         return false;
     }
-    if (J.items)
+    if (J.items) {
         cp_async_wait_all();
-    else
+        R.item[slot] = *pre;
+    } else {
         R.item[slot] = J.item0;
+    }
     const Item I = R.item[slot];
     R.chunk[slot] = c;
     R.itidx[slot] = it;
@@ -591,6 +593,8 @@ __device__ __forceinline__ void exit_job(const Job &J, uint32_t epoch)
 {
     __threadfence();
     if (atomicAdd(J.exit_count, 1u) != gridDim.x - 1) return;
+    __threadfence();   // every other CTA's accounting is visible
+    if (!J.items) finalize_item(J, 0, J.item0);
     const unsigned int claims = atomicExch(J.claim, 0u);
     const unsigned int flags = atomicAdd(J.flags, 0u);
     if (claims != J.total_chunks + gridDim.x || flags != 0) {
@@ -619,18 +623,27 @@ __device__ __forceinline__ void exit_job(const Job &J, uint32_t epoch)
 
 // Warps 0-7 (compute): at iteration i, wait for chunk i's stage, classify and
 // count it, scan, publish its aggregate and hand it to the look-back warp
-// (pend_bar). Then write out chunk i-2 from staging buffer i&1 (its offset was
-// computed meanwhile) and signal it (written_bar), and assemble chunk i's
-// output into the same buffer. Thread 0 also feeds the TMA ring, claiming
-// chunk ids one iteration ahead so that the claim's latency is hidden.
-// Warp 8 (look-back): for every handed-over chunk, as soon as its aggregate
-// is out, look back, publish the inclusive prefix and hand the offset back
-// (excl_bar); once the chunk is written, record its first error and count it
-// done, finishing its item's result when it is the item's last chunk. None of
-// the global atomics and fences of this bookkeeping sit on the compute path.
-// Hand-over slots and their barriers come in fours (chunk j uses j&3): the
-// compute warps may hand over chunk j+2 before the look-back warp took
-// chunk j.
+// (pend_bar). Then write out chunk i-kDepth from staging buffer i % kDepth
+// (its offset was computed meanwhile) and signal it (written_bar), and
+// assemble chunk i's output into the same buffer. Thread 0 also feeds the TMA
+// ring, claiming chunk ids one iteration ahead so that the claim's latency is
+// hidden. Warp 8 (look-back): for every handed-over chunk, as soon as its
+// aggregate is out, look back, publish the inclusive prefix and hand the
+// offset back (excl_bar); once the chunk is written, record its first error
+// and count it done, finishing its item's result when it is the item's last
+// chunk (a one-item job is finished by its last CTA). None of the global
+// atomics and fences of this bookkeeping sit on the compute path.
+// Output staging depth: a chunk staged in iteration i is written out in
+// iteration i + kDepth, so its offset has kDepth iterations to arrive.
+#ifndef GBU_OUT_DEPTH
+#define GBU_OUT_DEPTH 3
+#endif
+constexpr int kDepth = GBU_OUT_DEPTH;
+// Hand-over slots (chunk j uses j % kSlots): more than the kDepth + 1
+// chunks between a hand-over and the write-out that retires it.
+constexpr int kSlots = 8;
+static_assert(kSlots > kDepth + 1, "hand-over slots");
+
 template <bool kWrite, int kLook>
 __global__ void __launch_bounds__(kBlock, kMinBlocks)
 transcode_kernel(const Job J)
@@ -638,22 +651,23 @@ transcode_kernel(const Job J)
     extern __shared__ __align__(128) uint8_t dyn_smem[];
     uint8_t *const stages = dyn_smem;
     uint8_t *const obufs = dyn_smem + kStages * kStageBytes;
-    __shared__ __align__(8) Ring R;
-    __shared__ __align__(8) uint64_t pend_bar[4], excl_bar[4], written_bar[4];
-    __shared__ Pending s_pend[4];
-    __shared__ unsigned long long s_excl[4], s_errsnap[4], s_err[2];
+    __shared__ __align__(16) Ring R;
+    __shared__ __align__(16) Item s_next_item;
+    __shared__ __align__(8) uint64_t pend_bar[kSlots], excl_bar[kSlots], written_bar[kSlots];
+    __shared__ Pending s_pend[kSlots];
+    __shared__ unsigned long long s_excl[kSlots], s_errsnap[kSlots], s_err[kDepth];
     __shared__ uint32_t s_warp[kThreads / 32 + 1];
     __shared__ uint32_t s_epoch;
 
     const uint32_t tid = threadIdx.x;
     if (tid == 0) {
         for (int s = 0; s < kStages; s++) mbar_init(&R.full[s], 1);
-        for (int s = 0; s < 4; s++) {
+        for (int s = 0; s < kSlots; s++) {
             mbar_init(&pend_bar[s], 1);
             mbar_init(&excl_bar[s], 1);
             mbar_init(&written_bar[s], 1);
         }
-        s_err[0] = s_err[1] = ~0ull;
+        for (int s = 0; s < kDepth; s++) s_err[s] = ~0ull;
         fence_mbar_init();
         s_epoch = *reinterpret_cast<volatile unsigned int *>(J.epoch);
     }
@@ -664,13 +678,19 @@ transcode_kernel(const Job J)
         // ---- look-back warp -------------------------------------------------
         const bool lead = tid == kThreads;
         bool failed = false;
-        Done d1{}, d2{};   // chunks j-1 and j-2
+        Done dq[kDepth] = {};   // dq[m]: chunk j-1-m
         // chunk j was written: merge its first error, count it done
         auto account = [&](const Done &d, uint32_t j) -> bool {
-            if (!mbar_wait(&written_bar[j & 3], (j >> 2) & 1u)) return false;
+            if (!mbar_wait(&written_bar[j % kSlots], (j / kSlots) & 1u)) return false;
             if (lead) {
-                const uint64_t key = s_errsnap[j & 3];
-                if (d.nchunks == 1) {
+                const uint64_t key = s_errsnap[j % kSlots];
+                if (!J.items) {
+                    // one item: its result is finished by the last CTA out
+                    if (key != ~0ull) {
+                        J.err_prefix[d.chunk] = d.excl + (key & 0x7FFFu);
+                        atomicMin(&J.item_err[0], ((key >> 23) << 8) | ((key >> 15) & 0xFFu));
+                    }
+                } else if (d.nchunks == 1) {
                     finalize_single(J, J.items ? J.items[d.itidx] : J.item0, d.agg, key);
                 } else {
                     if (key != ~0ull) {
@@ -685,8 +705,8 @@ transcode_kernel(const Job J)
         };
         uint32_t j = 0;
         for (;; j++) {
-            const int q = j & 3;
-            if (!mbar_wait(&pend_bar[q], (j >> 2) & 1u)) {
+            const int q = j % kSlots;
+            if (!mbar_wait(&pend_bar[q], (j / kSlots) & 1u)) {
                 failed = true;
                 break;
             }
@@ -710,16 +730,18 @@ transcode_kernel(const Job J)
                 s_excl[q] = excl;
                 mbar_arrive(&excl_bar[q]);
             }
-            if (j >= 2 && !account(d2, j - 2)) {
+            if (j >= kDepth && !account(dq[kDepth - 1], j - kDepth)) {
                 failed = true;
                 break;
             }
-            d2 = d1;
-            d1 = d0;
+#pragma unroll
+            for (int m = kDepth - 1; m > 0; m--) dq[m] = dq[m - 1];
+            dq[0] = d0;
         }
-        // the compute warps stop after writing out the last two chunks
-        if (!failed && j >= 2 && !account(d2, j - 2)) failed = true;
-        if (!failed && j >= 1 && !account(d1, j - 1)) failed = true;
+        // the compute warps stop after writing out their last kDepth chunks
+#pragma unroll
+        for (int m = kDepth; m > 0; m--)
+            if (!failed && j >= (uint32_t)m && !account(dq[m - 1], j - m)) failed = true;
         if (lead) {
             if (failed) atomicOr(J.flags, 1u);
             exit_job(J, epoch);
@@ -731,8 +753,8 @@ transcode_kernel(const Job J)
     // write out chunk j (staging buffer j&1) once its offset is known; false
     // if the wait for the offset gave up
     auto write_out = [&](uint32_t j) -> bool {
-        const int q = j & 3;
-        if (!mbar_wait(&excl_bar[q], (j >> 2) & 1u)) return false;
+        const int q = j % kSlots;
+        if (!mbar_wait(&excl_bar[q], (j / kSlots) & 1u)) return false;
         if (kWrite) {
             const Pending &P = s_pend[q];
             const uint64_t excl = s_excl[q];
@@ -743,13 +765,13 @@ transcode_kernel(const Job J)
                 const uint64_t room = P.item.cap - excl;
                 uint32_t nw = P.agg < stage_units ? P.agg : stage_units;
                 if (nw > room) nw = (uint32_t)room;
-                block_store_bytes(obufs + (size_t)(j & 1) * kOutBufBytes, P.item.out + excl * ub,
+                block_store_bytes(obufs + (size_t)(j % kDepth) * kOutBufBytes, P.item.out + excl * ub,
                                   nw * ub);
             }
         }
         if (tid == 0) {
-            s_errsnap[q] = s_err[j & 1];
-            s_err[j & 1] = ~0ull;
+            s_errsnap[q] = s_err[j % kDepth];
+            s_err[j % kDepth] = ~0ull;
             mbar_arrive(&written_bar[q]);
         }
         return true;
@@ -764,11 +786,11 @@ transcode_kernel(const Job J)
     auto fetch_it = [&]() {
         if (J.chunk_item && next_claim < J.total_chunks) next_it = J.chunk_item[next_claim];
     };
-    // the descriptor goes straight into the ring slot of the next load
-    auto fetch_item = [&](int slot) {
+    // the descriptor of the next load, fetched asynchronously
+    auto fetch_item = [&]() {
         if (J.items && next_claim < J.total_chunks) {
             const uint8_t *src = reinterpret_cast<const uint8_t *>(J.items + next_it);
-            uint8_t *dst = reinterpret_cast<uint8_t *>(&R.item[slot]);
+            uint8_t *dst = reinterpret_cast<uint8_t *>(&s_next_item);
 #pragma unroll
             for (int q = 0; q < (int)sizeof(Item); q += 16) cp_async16(dst + q, src + q);
         }
@@ -777,13 +799,13 @@ transcode_kernel(const Job J)
         for (int s = 0; s < kStages - 1 && producing; s++) {
             next_claim = atomicAdd(J.claim, 1u);
             fetch_it();
-            fetch_item(s);
-            producing = produce(J, next_claim, next_it, s, stages, R);
+            fetch_item();
+            producing = produce(J, next_claim, next_it, &s_next_item, s, stages, R);
         }
-        if (producing) {   // the chunk loaded at the top of iteration 0
+        if (producing) {   // the chunk loaded in iteration 0
             next_claim = atomicAdd(J.claim, 1u);
             fetch_it();
-            fetch_item(kStages - 1);
+            fetch_item();
         }
     }
 
@@ -791,15 +813,18 @@ transcode_kernel(const Job J)
     bool failed = false;
     while (true) {
         const int slot = iter % kStages;
-        const int p = iter & 1;
-        if (tid == 0 && producing) {
-            producing = produce(J, next_claim, next_it, (iter + kStages - 1) % kStages, stages, R);
-            if (producing) next_claim = atomicAdd(J.claim, 1u);   // used next iteration
-        }
+        const int p = iter % kDepth;
         const bool ok = mbar_wait(&R.full[slot], (iter / kStages) & 1u);
         if (cw_sync_or(!ok)) {
             failed = true;
             break;
+        }
+        // every compute thread is done with iteration iter-1: its stage can
+        // be refilled
+        if (tid == 0 && producing) {
+            producing = produce(J, next_claim, next_it, &s_next_item, (iter + kStages - 1) % kStages,
+                                stages, R);
+            if (producing) next_claim = atomicAdd(J.claim, 1u);   // used next iteration
         }
         if (R.end[slot]) break;
         const Item I = R.item[slot];
@@ -813,13 +838,13 @@ transcode_kernel(const Job J)
         auto hand_over = [&]() {
             if (tid == 0) {
                 st_relaxed(&J.status[c], pack_status(k == 0 ? kFlagInclusive : kFlagAggregate, epoch, agg));
-                Pending &P = s_pend[iter & 3];
+                Pending &P = s_pend[iter % kSlots];
                 P.item = I;
                 P.chunk = c;
                 P.itidx = it;
                 P.agg = agg;
                 P.end = 0;
-                mbar_arrive(&pend_bar[iter & 3]);
+                mbar_arrive(&pend_bar[iter % kSlots]);
                 if (producing) fetch_it();
             }
             handed++;
@@ -830,7 +855,7 @@ transcode_kernel(const Job J)
             const uint32_t cnt = chunk16_phase1(st, stage, vt, lo, hi);
             t_off = block_exclusive_scan(cnt, s_warp, &agg);
             hand_over();
-            if (iter >= 2 && cw_sync_or(!write_out(iter - 2))) {
+            if (iter >= kDepth && cw_sync_or(!write_out(iter - kDepth))) {
                 failed = true;
                 break;
             }
@@ -841,7 +866,7 @@ transcode_kernel(const Job J)
             const uint32_t cnt = chunk8_phase1(st, stage, vt, lo, hi);
             t_off = block_exclusive_scan(cnt, s_warp, &agg);
             hand_over();
-            if (iter >= 2 && cw_sync_or(!write_out(iter - 2))) {
+            if (iter >= kDepth && cw_sync_or(!write_out(iter - kDepth))) {
                 failed = true;
                 break;
             }
@@ -849,18 +874,17 @@ transcode_kernel(const Job J)
         }
         // every thread read this iteration's R.item[slot] at its start: the
         // slot's descriptor can be replaced by the one the next load needs
-        if (tid == 0 && producing) fetch_item(slot);
-        cw_sync();
+        if (tid == 0 && producing) fetch_item();
         iter++;
     }
-    // drain: write out the last two chunks, then stop the look-back warp
-    if (!failed && iter >= 2 && cw_sync_or(!write_out(iter - 2))) failed = true;
-    if (!failed && iter >= 1 && cw_sync_or(!write_out(iter - 1))) failed = true;
+    // drain: write out the last kDepth chunks, then stop the look-back warp
+    for (int m = kDepth; m > 0 && !failed; m--)
+        if (iter >= (uint32_t)m && cw_sync_or(!write_out(iter - m))) failed = true;
     if (tid == 0) {
         if (failed) atomicOr(J.flags, 1u);
-        Pending &P = s_pend[handed & 3];
+        Pending &P = s_pend[handed % kSlots];
         P.end = 1;
-        mbar_arrive(&pend_bar[handed & 3]);
+        mbar_arrive(&pend_bar[handed % kSlots]);
     }
 }
 
@@ -871,7 +895,7 @@ int g_sms[64] = {0};
 
 size_t job_smem_bytes(bool write)
 {
-    return (size_t)kStages * kStageBytes + (write ? 2 * (size_t)kOutBufBytes : 0);
+    return (size_t)kStages * kStageBytes + (write ? (size_t)kDepth * kOutBufBytes : 0);
 }
 
 // Every instantiation of the kernel: (write, look-back width).

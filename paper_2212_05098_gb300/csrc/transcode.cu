@@ -386,9 +386,9 @@ __device__ __forceinline__ uint32_t enc3(uint32_t u)
 struct St16 {
     uint32_t w[10];    // w[0]: words -2,-1; w[1..8]: own words 0..15; w[9]: words 16,17
     uint32_t vmask;
-    bool edge;         // the thread's words straddle an end of the input
+    bool slow;         // the thread straddles an end of the input
     bool skip;         // the whole warp lies outside the input (warp-uniform)
-    bool general, only12;
+    bool sur, only12;  // the warp holds surrogates / only words below U+0800 (warp-uniform)
 };
 
 __device__ __forceinline__ uint32_t unit_keep(int64_t u, int64_t lo, int64_t hi)
@@ -411,10 +411,10 @@ __device__ __forceinline__ uint32_t chunk16_phase1(St16 &st, const uint8_t *stag
     // skips the chunk body
     const bool outside = vt + 16 <= lo || vt >= hi;
     st.skip = __all_sync(kFull, outside);
-    st.edge = false;
+    bool edge = false;
     if (st.skip) {
         st.vmask = 0;
-        st.general = st.only12 = false;
+        st.slow = st.sur = st.only12 = false;
         return 0;
     }
     st.vmask = 0xFFFFu;
@@ -425,7 +425,7 @@ __device__ __forceinline__ uint32_t chunk16_phase1(St16 &st, const uint8_t *stag
         st.vmask = 0;
         masked = true;
     } else if (vt < lo || vt + 16 > hi) {   // straddles an end of the input
-        st.edge = masked = true;
+        edge = masked = true;
         st.vmask = 0;
 #pragma unroll
         for (int i = 0; i < 16; i++)
@@ -453,8 +453,9 @@ __device__ __forceinline__ uint32_t chunk16_phase1(St16 &st, const uint8_t *stag
         any800 |= gb;
         anysur |= s;
     }
-    st.general = __any_sync(kFull, anysur != 0 || st.edge);
+    st.sur = __any_sync(kFull, anysur != 0);
     st.only12 = !__any_sync(kFull, any800 != 0);
+    st.slow = edge;
     return cnt;
 }
 
@@ -462,13 +463,54 @@ template <bool kWrite>
 __device__ __forceinline__ void chunk16_phase2(const St16 &st, uint8_t *obuf, uint32_t t_off,
                                                int64_t vt, int64_t lo, unsigned long long *s_err)
 {
-    if (st.skip) return;
+    if (st.skip || st.vmask == 0) return;   // nothing of the input here
     const uint32_t *w = st.w;
-    if (!st.general) {
-        // no surrogates in this warp: every word is valid
+    bool slow = st.slow;
+    if (st.sur && !slow) {
+        // sequencing (Sec. 7.4): every high surrogate is followed by a low
+        // one and every low one preceded by a high one; a thread holding a
+        // lone one takes the exact path below
+        auto hi_lanes = [](uint32_t x) { return surr_lanes(x) & ~(x << 5); };
+        auto lo_lanes = [](uint32_t x) { return surr_lanes(x) & (x << 5); };
+        uint32_t v = 0, h_prev = hi_lanes(w[0]), h_cur = hi_lanes(w[1]), l_cur = lo_lanes(w[1]);
+#pragma unroll
+        for (int j = 1; j <= 8; j++) {
+            const uint32_t l_next = lo_lanes(w[j + 1]);
+            v |= (h_cur & ~__funnelshift_r(l_cur, l_next, 16)) |
+                 (l_cur & ~__funnelshift_l(h_prev, h_cur, 16));
+            h_prev = h_cur;
+            h_cur = hi_lanes(w[j + 1]);
+            l_cur = l_next;
+        }
+        slow = v != 0;
+    }
+    if (!slow) {
+        // every word of this thread is valid
         if (!kWrite) return;
         uint8_t *p = obuf + t_off;
-        if (st.only12) {
+        if (st.sur) {
+            // surrogate pairs: the high one emits the pair's 4 bytes, the
+            // low one nothing
+#pragma unroll
+            for (int i = 0; i < 16; i++) {
+                const uint32_t u = lane16(w, i), nx = lane16(w, i + 1);
+                const uint32_t t = u & 0xFC00u;
+                const bool is_hi = t == 0xD800u, is_lo = t == 0xDC00u;
+                const bool c2 = u >= 0x80u, c3 = u >= 0x800u;
+                uint32_t v = c3 ? enc3(u) : (c2 ? enc2(u) : u);
+                if (is_hi) {
+                    const uint32_t cp = (u << 10) + nx + 0xFCA02400u;
+                    v = (cp >> 18) | ((cp >> 4) & 0x3F00u) | ((cp << 10) & 0x3F0000u) |
+                        ((cp << 24) & 0x3F000000u) | 0x808080F0u;
+                }
+                const uint32_t len = is_lo ? 0u : (is_hi ? 4u : 1u + (c2 ? 1u : 0u) + (c3 ? 1u : 0u));
+                if (len >= 1) p[0] = (uint8_t)v;
+                if (len >= 2) p[1] = (uint8_t)(v >> 8);
+                if (len >= 3) p[2] = (uint8_t)(v >> 16);
+                if (len >= 4) p[3] = (uint8_t)(v >> 24);
+                p += len;
+            }
+        } else if (st.only12) {
 #pragma unroll
             for (int i = 0; i < 16; i++) {
                 const uint32_t u = lane16(w, i);

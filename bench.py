@@ -181,6 +181,21 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(inside)}
 
 
+def job_rate(local_bytes: float, local_ms: float, world: int, device) -> tuple[float, float]:
+    """Whole-job throughput: every rank's bytes over the slowest rank's time.
+    Returns (GB/s, slowest time in ms). With world > 1 it all-reduces (SUM of
+    bytes, MAX of times) over the default process group."""
+    import torch
+    b = torch.tensor([float(local_bytes)], dtype=torch.float64, device=device)
+    m = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(b, op=dist.ReduceOp.SUM)
+        dist.all_reduce(m, op=dist.ReduceOp.MAX)
+    ms = float(m.item())
+    return float(b.item()) / (ms / 1e3) / 1e9, ms
+
+
 def gen_inputs(profiles, size, rank, pool):
     cases = []
     for prof in profiles:
@@ -339,16 +354,10 @@ def main():
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    ms_total = start.elapsed_time(end)
-    ms = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(ms, op=dist.ReduceOp.MAX)
-    ms_total = float(ms.item())
+    bytes_step = sum(c["data"].size for c in cases)
+    value, ms_total = job_rate(bytes_step * K, start.elapsed_time(end), world, "cuda")
     sampler.stop()
     clocks = sampler.summary(t_wall0, t_wall1)
-
-    bytes_step = sum(c["data"].size for c in cases)
-    value = world * bytes_step * K / (ms_total / 1e3) / 1e9
 
     # the kernel's roofline over all its launches, with a per-direction split
     peak, peak_src = measured_peak()
@@ -551,11 +560,7 @@ def run_batched(args, rank, world, local):
     sampler.stop()
     clocks = sampler.summary(t_wall0, t_wall1)
     ms_list = [a.elapsed_time(b) for a, b in ev]
-    ms = torch.tensor([sum(ms_list)], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(ms, op=dist.ReduceOp.MAX)
-    ms_total = float(ms.item())
-    value = world * in_bytes * K / (ms_total / 1e3) / 1e9
+    value, ms_total = job_rate(in_bytes * K, sum(ms_list), world, "cuda")
 
     # the same strings, one plain-kernel launch each (default launch parameters)
     plain = gbu.Context(local)

@@ -198,62 +198,56 @@ __device__ __forceinline__ uint64_t lookback(const unsigned long long *status, u
                                              uint32_t epoch, unsigned int *flags)
 {
     const int lane = threadIdx.x & 31;
+    // before the item's first chunk: an inclusive prefix of 0
+    const uint64_t start = pack_status(kFlagInclusive, epoch, 0);
     uint64_t excl = 0;
     int64_t base = (int64_t)k - 1;
     uint32_t rounds = 0;
     while (true) {
-        uint64_t val[kLook];
-        uint32_t inc[kLook], nr[kLook];
-        while (true) {
-#pragma unroll
-            for (int m = 0; m < kLook; m++) {
-                const int64_t idx = base - 32 * m - lane;
-                uint64_t flag = kFlagInclusive;   // before the item's first chunk: inclusive 0
-                val[m] = 0;
-                if (idx >= 0) {
-                    const uint64_t w = ld_relaxed(&status[idx]);
-                    flag = w >> 62;
-                    if (((w >> kEpochShift) & kEpochMask) != epoch) flag = 0;
-                    val[m] = w & kValueMask;
-                }
-                inc[m] = __ballot_sync(kFull, flag == kFlagInclusive);
-                nr[m] = __ballot_sync(kFull, flag == 0);
-            }
-            // ready when no word before the nearest inclusive one is missing
-            bool ready = true, found = false;
-#pragma unroll
-            for (int m = 0; m < kLook; m++) {
-                if (found) break;
-                const uint32_t upto = inc[m] ? ((inc[m] & (0u - inc[m])) - 1u) : 0xFFFFFFFFu;
-                if (nr[m] & upto) ready = false;
-                if (inc[m]) found = true;
-            }
-            if (ready) break;
-            ++rounds;
-            const bool other = (rounds & 63u) == 0 &&
-                               *reinterpret_cast<volatile unsigned int *>(flags) != 0;
-            if (rounds > kSpinLimit || __any_sync(kFull, other)) {
-                if (lane == 0) atomicOr(flags, 1u);
-                return excl;
-            }
-            __nanosleep(rounds < 8 ? 32 : 256);
-        }
-        uint64_t part = 0;
-        bool found = false;
+        // one round trip for the whole window, then one pass over it from the
+        // nearest predecessor backwards (only the raw words stay in registers)
+        uint64_t w[kLook];
 #pragma unroll
         for (int m = 0; m < kLook; m++) {
-            if (found) break;
-            if (inc[m]) {
-                const int l = __ffs(inc[m]) - 1;    // nearest predecessor with a full prefix
-                if (lane <= l) part += val[m];
+            const int64_t idx = base - 32 * m - lane;
+            w[m] = idx >= 0 ? ld_relaxed(&status[idx]) : start;
+        }
+        bool ready = true, found = false;
+        uint64_t part = 0;
+#pragma unroll
+        for (int m = 0; m < kLook; m++) {
+            if (found) break;                        // warp-uniform
+            const uint64_t x = w[m];
+            const bool current = ((x >> kEpochShift) & kEpochMask) == epoch;
+            const uint64_t flag = current ? x >> 62 : 0;
+            const uint32_t inc = __ballot_sync(kFull, flag == kFlagInclusive);
+            const uint32_t nr = __ballot_sync(kFull, flag == 0);
+            // ready when no word before the nearest inclusive one is missing
+            const uint32_t upto = inc ? ((inc & (0u - inc)) - 1u) : 0xFFFFFFFFu;
+            if (nr & upto) ready = false;
+            const uint64_t v = x & kValueMask;
+            if (inc) {
+                const int l = __ffs(inc) - 1;          // nearest predecessor with a full prefix
+                if (lane <= l) part += v;
                 found = true;
             } else {
-                part += val[m];
+                part += v;
             }
         }
-        excl += warp_sum_u64(part);
-        if (found) return excl;
-        base -= 32 * kLook;
+        if (ready) {
+            excl += warp_sum_u64(part);
+            if (found) return excl;
+            base -= 32 * kLook;
+            continue;
+        }
+        ++rounds;
+        const bool other = (rounds & 63u) == 0 &&
+                           *reinterpret_cast<volatile unsigned int *>(flags) != 0;
+        if (rounds > kSpinLimit || __any_sync(kFull, other)) {
+            if (lane == 0) atomicOr(flags, 1u);
+            return excl;
+        }
+        __nanosleep(rounds < 8 ? 32 : 256);
     }
 }
 

@@ -950,9 +950,10 @@ constexpr const void *kernel_fn()
 const void *kernel_for(bool write, int look)
 {
     switch (look) {
-    case 4: return write ? kernel_fn<true, 4>() : kernel_fn<false, 4>();
+    case 2: return write ? kernel_fn<true, 2>() : kernel_fn<false, 2>();
+    case 8: return write ? kernel_fn<true, 8>() : kernel_fn<false, 8>();
     case 16: return write ? kernel_fn<true, 16>() : kernel_fn<false, 16>();
-    default: return write ? kernel_fn<true, 8>() : kernel_fn<false, 8>();
+    default: return write ? kernel_fn<true, 4>() : kernel_fn<false, 4>();
     }
 }
 
@@ -968,7 +969,7 @@ int job_max_ctas_per_sm(int device)
             if (cudaFuncSetAttribute(kernel_for(w != 0, look), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)job_smem_bytes(w != 0)) != cudaSuccess)
                 return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel_for(true, 8), kBlock,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel_for(true, GBU_DEFAULT_LOOK), kBlock,
                                                       job_smem_bytes(true)) != cudaSuccess ||
         per < 1)
         per = 1;

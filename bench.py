@@ -63,10 +63,12 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=256 << 20,
                     help="bytes of each buffer the oracle baseline transcodes")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["single", "batched", "serving"], default="single",
+    ap.add_argument("--workload", choices=["single", "batched", "serving", "latency"],
+                    default="single",
                     help="single: 4 profiles x 2 directions x one buffer each (default); "
                          "batched: many strings in one persistent graph-captured launch; "
-                         "serving: Poisson request arrivals through the serving loop")
+                         "serving: Poisson request arrivals through the serving loop; "
+                         "latency: one call's latency and throughput against input size")
     ap.add_argument("--strings", type=int, default=200_000, help="batched: number of strings")
     ap.add_argument("--rates", default="0.1,0.25,0.5,0.75,0.9,1.0,1.2",
                     help="serving: arrival rates as fractions of the plain kernel's GB/s")
@@ -271,6 +273,9 @@ def main():
     if args.workload == "serving":
         run_serving(args, rank, world, local)
         return
+    if args.workload == "latency":
+        run_latency(args, rank, world, local)
+        return
     # process pool for the generator: started before the first CUDA call
     pool = textgen.process_pool() if args.size >= (64 << 20) else None
 
@@ -429,6 +434,23 @@ def main():
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "steps": args.e2e_steps, "api": "gbu_*_host (pinned host buffers)"}
 
+    # validation only (no output, no look-back), same buffers, 3 passes
+    vres = torch.zeros(4, dtype=torch.int64, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(3):
+            for c in cases:
+                if c["dir"] == "utf8_to_utf16le":
+                    gbu.gbu_validate_utf8_async(ctx.handle, c["d_in"].data_ptr(), c["n"],
+                                                vres.data_ptr(), sh)
+                else:
+                    gbu.gbu_validate_utf16le_async(ctx.handle, c["d_in"].data_ptr(), c["n"],
+                                                   vres.data_ptr(), sh)
+        e1.record(stream)
+    stream.synchronize()
+    validate_gbs = 3 * bytes_step / (e0.elapsed_time(e1) / 1e3) / 1e9
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         b, dt = cpu_baseline(cases, args.cpu_sample)
@@ -452,6 +474,7 @@ def main():
             "roofline": roofline,
             "directions": directions,
             "per_buffer_input_gbs": per_case,
+            "validate_only_input_gbs": validate_gbs,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clocks,
@@ -808,6 +831,83 @@ def run_serving(args, rank, world, local):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+LATENCY_METRIC = "latency of one validated transcoding call against input size (mix profile)"
+
+
+def run_latency(args, rank, world, local):
+    """Small-string regime (the paper's throughput against input length,
+    Sec. 8): for input sizes 16 B .. 256 MiB of the mix profile, the median
+    device time of one asynchronous call (CUDA events) and the wall time of
+    one synchronous call (launch, wait, read the result), per direction."""
+    import torch
+
+    import paper_2212_05098_gb300 as gbu
+    torch.cuda.set_device(local)
+    top = min(args.size, 256 << 20)
+    t8 = textgen.generate("mix", top, textgen.UTF8, seed=0, keep_cps=False, keep_lens=False).data
+    t16 = textgen.generate("mix", top, textgen.UTF16, seed=0, keep_cps=False, keep_lens=False).data
+    gbu.load()
+    ctx = gbu.Context(local)
+    ctx.reserve(top)
+    d8, d16 = torch.from_numpy(t8).cuda(), torch.from_numpy(t16).cuda()
+    out = torch.empty(2 * top + 64, dtype=torch.uint8, device="cuda")
+    res = torch.zeros(4, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.Stream()
+    sh = stream.cuda_stream
+    rows = []
+    size = 16
+    while size <= top:
+        for direction, d in (("utf8_to_utf16le", d8), ("utf16le_to_utf8", d16)):
+            n = size if direction == "utf8_to_utf16le" else size // 2
+
+            def call_async():
+                if direction == "utf8_to_utf16le":
+                    gbu.gbu_utf8_to_utf16le_async(ctx.handle, d.data_ptr(), n, out.data_ptr(), n,
+                                                  res.data_ptr(), sh)
+                else:
+                    gbu.gbu_utf16le_to_utf8_async(ctx.handle, d.data_ptr(), n, out.data_ptr(),
+                                                  3 * n, res.data_ptr(), sh)
+
+            def call_sync():
+                if direction == "utf8_to_utf16le":
+                    return gbu.gbu_utf8_to_utf16le(ctx.handle, d.data_ptr(), n, out.data_ptr(), n, sh)
+                return gbu.gbu_utf16le_to_utf8(ctx.handle, d.data_ptr(), n, out.data_ptr(), 3 * n, sh)
+
+            reps = 20 if size <= (16 << 20) else 5
+            for _ in range(3):
+                call_async()
+            stream.synchronize()
+            dev = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                call_async()
+                e1.record(stream)
+                stream.synchronize()
+                dev.append(e0.elapsed_time(e1))
+            wall = []
+            for _ in range(reps):
+                t0 = time.perf_counter()
+                r = call_sync()
+                wall.append(time.perf_counter() - t0)
+            dev_ms = statistics.median(dev)
+            rows.append({"bytes": size, "direction": direction, "status": r.status,
+                         "device_us": dev_ms * 1e3, "sync_call_us": statistics.median(wall) * 1e6,
+                         "device_gbs": size / (dev_ms / 1e3) / 1e9})
+        size *= 4
+    big = [r for r in rows if r["bytes"] == rows[-1]["bytes"]]
+    if rank == 0:
+        line = {"metric": LATENCY_METRIC, "value": min(r["sync_call_us"] for r in rows),
+                "unit": "us (smallest synchronous call)", "n_gpus": world, "steps": len(rows),
+                "warmup": 3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+                "dtype": "u8+u16", "data": "synthetic (mix profile, seed 0)",
+                "config": {"workload": "one call per size, 16 B to 256 MiB by factors of 4",
+                           "largest_gbs": {r["direction"]: r["device_gbs"] for r in big}},
+                "sizes": rows, "gpu_launches": None}
+        print(json.dumps(line), flush=True)
+    ctx.close()
 
 
 def _host_call(gbu, ctx, c, outs, sh):

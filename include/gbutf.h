@@ -112,6 +112,14 @@ gbu_result gbu_utf16_length_from_utf8(gbu_ctx *ctx, const uint8_t *d_in, uint64_
 gbu_result gbu_utf8_length_from_utf16le(gbu_ctx *ctx, const uint16_t *d_in, uint64_t n_units,
                                         void *stream);
 
+/* Validation only (the paper's validation, Sec. 6.4 and 7.4, without the
+ * transcoding): status and in_offset as for the transcoding calls (the
+ * first invalid unit), out_len always 0. No output offsets are computed, so
+ * the chunks' look-back is skipped. */
+gbu_result gbu_validate_utf8(gbu_ctx *ctx, const uint8_t *d_in, uint64_t n_bytes, void *stream);
+gbu_result gbu_validate_utf16le(gbu_ctx *ctx, const uint16_t *d_in, uint64_t n_units,
+                                void *stream);
+
 /* Asynchronous forms: enqueue the work on `stream` and return at once. The
  * gbu_result is stored to `result` (device memory, or pinned host memory
  * mapped into the device's address space) when the stream reaches the end of
@@ -128,6 +136,10 @@ int32_t gbu_utf16_length_from_utf8_async(gbu_ctx *ctx, const uint8_t *d_in, uint
 int32_t gbu_utf8_length_from_utf16le_async(gbu_ctx *ctx, const uint16_t *d_in,
                                            uint64_t n_units, gbu_result *result,
                                            void *stream);
+int32_t gbu_validate_utf8_async(gbu_ctx *ctx, const uint8_t *d_in, uint64_t n_bytes,
+                                gbu_result *result, void *stream);
+int32_t gbu_validate_utf16le_async(gbu_ctx *ctx, const uint16_t *d_in, uint64_t n_units,
+                                   gbu_result *result, void *stream);
 
 /* Host-buffer forms: h_in / h_out are host memory (pinned memory gives the
  * fastest copies). The call copies the input to device scratch owned by the

@@ -97,6 +97,10 @@ SIGNATURES = {
     "gbu_utf16le_to_utf8": (gbu_result, [_VP, _VP, _U64, _VP, _U64, _VP]),
     "gbu_utf16_length_from_utf8": (gbu_result, [_VP, _VP, _U64, _VP]),
     "gbu_utf8_length_from_utf16le": (gbu_result, [_VP, _VP, _U64, _VP]),
+    "gbu_validate_utf8": (gbu_result, [_VP, _VP, _U64, _VP]),
+    "gbu_validate_utf16le": (gbu_result, [_VP, _VP, _U64, _VP]),
+    "gbu_validate_utf8_async": (_I32, [_VP, _VP, _U64, _VP, _VP]),
+    "gbu_validate_utf16le_async": (_I32, [_VP, _VP, _U64, _VP, _VP]),
     "gbu_utf8_to_utf16le_async": (_I32, [_VP, _VP, _U64, _VP, _U64, _VP, _VP]),
     "gbu_utf16le_to_utf8_async": (_I32, [_VP, _VP, _U64, _VP, _U64, _VP, _VP]),
     "gbu_utf16_length_from_utf8_async": (_I32, [_VP, _VP, _U64, _VP, _VP]),
@@ -180,6 +184,22 @@ def gbu_utf16_length_from_utf8(ctx, d_in, n_bytes, stream=0) -> Result:
 
 def gbu_utf8_length_from_utf16le(ctx, d_in, n_units, stream=0) -> Result:
     return _res(load().gbu_utf8_length_from_utf16le(ctx, d_in, n_units, stream))
+
+
+def gbu_validate_utf8(ctx, d_in, n_bytes, stream=0) -> Result:
+    return _res(load().gbu_validate_utf8(ctx, d_in, n_bytes, stream))
+
+
+def gbu_validate_utf16le(ctx, d_in, n_units, stream=0) -> Result:
+    return _res(load().gbu_validate_utf16le(ctx, d_in, n_units, stream))
+
+
+def gbu_validate_utf8_async(ctx, d_in, n_bytes, d_result, stream=0) -> int:
+    return load().gbu_validate_utf8_async(ctx, d_in, n_bytes, d_result, stream)
+
+
+def gbu_validate_utf16le_async(ctx, d_in, n_units, d_result, stream=0) -> int:
+    return load().gbu_validate_utf16le_async(ctx, d_in, n_units, d_result, stream)
 
 
 def gbu_utf8_to_utf16le_async(ctx, d_in, n_bytes, d_out, cap_units, d_result, stream=0) -> int:

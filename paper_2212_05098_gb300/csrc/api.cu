@@ -115,9 +115,10 @@ int32_t ensure_scratch(gbu_ctx *c, uint64_t chunks, cudaStream_t stream)
 
 enum class Op { U8toU16, U16toU8 };
 
-// Enqueue one call; result goes to `dst` (device-visible).
+// Enqueue one call; result goes to `dst` (device-visible). `validate`: the
+// validation-only form (implies !write).
 int32_t enqueue(gbu_ctx *c, Op op, const void *in, uint64_t n, void *out, uint64_t cap,
-                bool write, ResultSlot *dst, cudaStream_t stream)
+                bool write, ResultSlot *dst, cudaStream_t stream, bool validate = false)
 {
     if (!c || !dst || (n && !in) || (write && cap && !out)) return GBU_INVALID_ARG;
     if (n >= kMaxUnits) return GBU_INVALID_ARG;
@@ -133,6 +134,7 @@ int32_t enqueue(gbu_ctx *c, Op op, const void *in, uint64_t n, void *out, uint64
     J.item0 = make_item(in, n, utf16, out, cap, write, dst, 0);
     J.num_items = 1;
     J.total_chunks = J.item0.nchunks;
+    J.validate = validate ? 1u : 0u;
     int32_t st = ensure_scratch(c, J.total_chunks, stream);
     if (st != GBU_OK) {
         c->dirty = true;
@@ -152,13 +154,13 @@ int32_t enqueue(gbu_ctx *c, Op op, const void *in, uint64_t n, void *out, uint64
 }
 
 gbu_result run_sync(gbu_ctx *c, Op op, const void *in, uint64_t n, void *out, uint64_t cap,
-                    bool write, void *stream)
+                    bool write, void *stream, bool validate = false)
 {
     if (!c) return make(GBU_INVALID_ARG);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (n == 0) return make(GBU_OK, 0, 0);
     int32_t st = enqueue(c, op, in, n, out, cap, write,
-                         reinterpret_cast<ResultSlot *>(c->d_result), s);
+                         reinterpret_cast<ResultSlot *>(c->d_result), s, validate);
     if (st != GBU_OK) return make(st);
     if (!ok(cudaStreamSynchronize(s))) {
         c->dirty = true;
@@ -241,6 +243,30 @@ gbu_result gbu_utf16le_to_utf8(gbu_ctx *c, const uint16_t *d_in, uint64_t n, uin
 gbu_result gbu_utf16_length_from_utf8(gbu_ctx *c, const uint8_t *d_in, uint64_t n, void *stream)
 {
     return run_sync(c, Op::U8toU16, d_in, n, nullptr, 0, false, stream);
+}
+
+gbu_result gbu_validate_utf8(gbu_ctx *c, const uint8_t *d_in, uint64_t n, void *stream)
+{
+    return run_sync(c, Op::U8toU16, d_in, n, nullptr, 0, false, stream, true);
+}
+
+gbu_result gbu_validate_utf16le(gbu_ctx *c, const uint16_t *d_in, uint64_t n, void *stream)
+{
+    return run_sync(c, Op::U16toU8, d_in, n, nullptr, 0, false, stream, true);
+}
+
+int32_t gbu_validate_utf8_async(gbu_ctx *c, const uint8_t *d_in, uint64_t n, gbu_result *d_result,
+                                void *stream)
+{
+    return enqueue(c, Op::U8toU16, d_in, n, nullptr, 0, false,
+                   reinterpret_cast<ResultSlot *>(d_result), static_cast<cudaStream_t>(stream), true);
+}
+
+int32_t gbu_validate_utf16le_async(gbu_ctx *c, const uint16_t *d_in, uint64_t n,
+                                   gbu_result *d_result, void *stream)
+{
+    return enqueue(c, Op::U16toU8, d_in, n, nullptr, 0, false,
+                   reinterpret_cast<ResultSlot *>(d_result), static_cast<cudaStream_t>(stream), true);
 }
 
 gbu_result gbu_utf8_length_from_utf16le(gbu_ctx *c, const uint16_t *d_in, uint64_t n,

@@ -120,6 +120,7 @@ struct Job {
     unsigned long long *err_prefix; // [total_chunks] output units before the chunk's first error
     unsigned long long *item_err;   // [num_items] (position << 8) | kind of the first error, ~0 if none
     unsigned int *item_done;        // [num_items] chunks written
+    uint32_t validate;              // 1: validation only (no look-back; out_len reported as 0)
 };
 
 __device__ __forceinline__ uint64_t ld_relaxed(const unsigned long long *p)
@@ -418,8 +419,10 @@ __device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t
 // One thread, after the item's last chunk was written: assemble the
 // gbu_result from the scan total and the first-error word, store it, and reset
 // the item's counters for the next launch.
-__device__ __forceinline__ void write_result(const Item &I, int32_t st, uint64_t off, uint64_t len)
+__device__ __forceinline__ void write_result(const Item &I, int32_t st, uint64_t off, uint64_t len,
+                                             bool validate = false)
 {
+    if (validate) len = 0;
     // No fence: results are read once the launch has completed.
     volatile ResultSlot *r = I.result;
     r->status = st;
@@ -454,7 +457,7 @@ __device__ __forceinline__ void finalize_item(const Job &J, uint32_t it, const I
         off = I.n;
         len = total;
     }
-    write_result(I, st, off, len);
+    write_result(I, st, off, len, J.validate != 0);
     J.item_done[it] = 0;
     st_relaxed(&J.item_err[it], ~0ull);
 }
@@ -465,14 +468,15 @@ __device__ __forceinline__ void finalize_single(const Job &J, const Item &I, uin
                                                 uint64_t key)
 {
     const unsigned int flags = *reinterpret_cast<volatile unsigned int *>(J.flags);
+    const bool v = J.validate != 0;
     if (flags & 2u)
         write_result(I, kDeviceError, 0, 0);
     else if (flags & 1u)
         write_result(I, kDeviceTimeout, 0, 0);
     else if (key != ~0ull)
-        write_result(I, (int32_t)((key >> 15) & 0xFFu), key >> 23, key & 0x7FFFu);
+        write_result(I, (int32_t)((key >> 15) & 0xFFu), key >> 23, key & 0x7FFFu, v);
     else
-        write_result(I, ((I.op & kOpWrite) && agg > I.cap) ? kOutputTooSmall : kOk, I.n, agg);
+        write_result(I, ((I.op & kOpWrite) && agg > I.cap) ? kOutputTooSmall : kOk, I.n, agg, v);
 }
 
 }  // namespace gbu

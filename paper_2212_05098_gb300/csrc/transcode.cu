@@ -756,7 +756,7 @@ transcode_kernel(const Job J)
             if (P.end) break;
             const uint32_t k = P.chunk - P.item.chunk_base;
             uint64_t excl = 0;
-            if (k > 0) {
+            if (k > 0 && !J.validate) {   // validation needs no offsets
                 excl = lookback<kLook>(J.status + P.item.chunk_base, k, epoch, J.flags);
                 if (lead)
                     st_relaxed(&J.status[P.chunk], pack_status(kFlagInclusive, epoch, excl + P.agg));

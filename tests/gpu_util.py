@@ -88,9 +88,12 @@ def check_u8(ctx, data: np.ndarray, cap_units=None, in_off=0, out_off=0):
         bad = int(np.nonzero(got != want)[0][0])
         raise AssertionError(f"output differs at byte {bad} of {2 * keep}")
     assert dout.guards_intact(), "write outside [0, cap)"
-    lr = gbu.gbu_utf16_length_from_utf8(ctx, DevIn(data, in_off).ptr, data.size, 0)
+    din = DevIn(data, in_off)
+    lr = gbu.gbu_utf16_length_from_utf8(ctx, din.ptr, data.size, 0)
     lref = oracle.utf16_length_from_utf8(data)
     assert triple(lr) == triple(lref), (triple(lr), triple(lref))
+    vr = gbu.gbu_validate_utf8(ctx, din.ptr, data.size, 0)
+    assert triple(vr) == (lref.status, lref.in_offset, 0), (triple(vr), triple(lref))
     return r
 
 
@@ -107,7 +110,10 @@ def check_u16(ctx, data: np.ndarray, cap_bytes=None, in_off=0, out_off=0):
         bad = int(np.nonzero(got != ref_out[:keep])[0][0])
         raise AssertionError(f"output differs at byte {bad} of {keep}")
     assert dout.guards_intact(), "write outside [0, cap)"
-    lr = gbu.gbu_utf8_length_from_utf16le(ctx, DevIn(data, in_off).ptr, data.size // 2, 0)
+    din = DevIn(data, in_off)
+    lr = gbu.gbu_utf8_length_from_utf16le(ctx, din.ptr, data.size // 2, 0)
     lref = oracle.utf8_length_from_utf16le(data)
     assert triple(lr) == triple(lref), (triple(lr), triple(lref))
+    vr = gbu.gbu_validate_utf16le(ctx, din.ptr, data.size // 2, 0)
+    assert triple(vr) == (lref.status, lref.in_offset, 0), (triple(vr), triple(lref))
     return r

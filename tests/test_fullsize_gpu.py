@@ -58,6 +58,9 @@ def test_one_gib_matches_oracle(env, profile, enc):
     assert (r.status, r.in_offset, r.out_len) == (ref.status, ref.in_offset, ref.out_len)
     want = torch.from_numpy(ref_out.view(np.uint8)).cuda()
     assert torch.equal(d_out[: ref.out_len * ub], want)
+    v = (gbu.gbu_validate_utf8(ctx, d_in.data_ptr(), n, 0) if enc == textgen.UTF8
+         else gbu.gbu_validate_utf16le(ctx, d_in.data_ptr(), n, 0))
+    assert (v.status, v.in_offset, v.out_len) == (ref.status, ref.in_offset, 0)
 
 
 @pytest.mark.parametrize("enc", [textgen.UTF8, textgen.UTF16])
@@ -85,6 +88,10 @@ def test_validation_stress_1000_cases(env, enc):
         d_in[lo:hi] = torch.from_numpy(p.data).cuda()
         r = _run(torch, ctx, enc, d_in, n, d_out, cap)
         assert (r.status, r.in_offset, r.out_len) == (p.kind, p.err_unit, p.prefix_out), (i, p.case)
+        if i % 10 == 0:   # validation-only call: same first error
+            v = (gbu.gbu_validate_utf8(ctx, d_in.data_ptr(), n, 0) if enc == textgen.UTF8
+                 else gbu.gbu_validate_utf16le(ctx, d_in.data_ptr(), n, 0))
+            assert (v.status, v.in_offset, v.out_len) == (p.kind, p.err_unit, 0), (i, p.case)
         # valid prefix: the unpatched text's output up to the window, then spaces
         w_out = int(outs[np.searchsorted(starts, lo // ub_in)]) * ub_out
         assert torch.equal(d_out[:w_out], base_dev[:w_out]), (i, p.case)

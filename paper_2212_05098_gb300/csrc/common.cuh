@@ -17,7 +17,10 @@
 
 namespace gbu {
 
-constexpr int kThreads = 256;                 // compute threads of a CTA
+#ifndef GBU_THREADS
+#define GBU_THREADS 256
+#endif
+constexpr int kThreads = GBU_THREADS;         // compute threads of a CTA
 constexpr int kBlock = kThreads + 32;         // + one look-back warp
 constexpr unsigned kFull = 0xffffffffu;
 
@@ -41,7 +44,7 @@ __device__ __forceinline__ bool cw_sync_or(bool v)
 
 // Every chunk is 8 KiB of input in both directions: 8192 UTF-8 bytes or 4096
 // UTF-16 words. Thread t always owns input bytes [32t, 32t + 32) of its chunk.
-constexpr uint32_t kChunkBytes = 8192;
+constexpr uint32_t kChunkBytes = 32 * kThreads;   // 8192 with 256 compute threads
 constexpr uint32_t kChunk8 = kChunkBytes;        // UTF-8 bytes per chunk
 constexpr uint32_t kChunk16 = kChunkBytes / 2;   // UTF-16 words per chunk
 // Input ring: each stage holds one chunk plus kHalo bytes on each side.

@@ -112,6 +112,25 @@ gbu_result gbu_utf16_length_from_utf8(gbu_ctx *ctx, const uint8_t *d_in, uint64_
 gbu_result gbu_utf8_length_from_utf16le(gbu_ctx *ctx, const uint16_t *d_in, uint64_t n_units,
                                         void *stream);
 
+/* UTF-16BE forms (the byte order the paper's Sec. 2.1 mentions beside
+ * UTF-16LE): identical to the UTF-16LE calls except that every UTF-16 word
+ * is read or written with its high byte first. d_in / d_out as for the
+ * UTF-16LE calls (2-byte aligned, units of words). */
+gbu_result gbu_utf8_to_utf16be(gbu_ctx *ctx, const uint8_t *d_in, uint64_t n_bytes,
+                               uint16_t *d_out, uint64_t cap_units, void *stream);
+gbu_result gbu_utf16be_to_utf8(gbu_ctx *ctx, const uint16_t *d_in, uint64_t n_units,
+                               uint8_t *d_out, uint64_t cap_bytes, void *stream);
+gbu_result gbu_utf8_length_from_utf16be(gbu_ctx *ctx, const uint16_t *d_in, uint64_t n_units,
+                                        void *stream);
+gbu_result gbu_validate_utf16be(gbu_ctx *ctx, const uint16_t *d_in, uint64_t n_units,
+                                void *stream);
+int32_t gbu_utf8_to_utf16be_async(gbu_ctx *ctx, const uint8_t *d_in, uint64_t n_bytes,
+                                  uint16_t *d_out, uint64_t cap_units, gbu_result *result,
+                                  void *stream);
+int32_t gbu_utf16be_to_utf8_async(gbu_ctx *ctx, const uint16_t *d_in, uint64_t n_units,
+                                  uint8_t *d_out, uint64_t cap_bytes, gbu_result *result,
+                                  void *stream);
+
 /* Validation only (the paper's validation, Sec. 6.4 and 7.4, without the
  * transcoding): status and in_offset as for the transcoding calls (the
  * first invalid unit), out_len always 0. No output offsets are computed, so
@@ -163,7 +182,10 @@ typedef enum gbu_op {
     GBU_OP_UTF8_TO_UTF16LE = 0,           /* as gbu_utf8_to_utf16le            */
     GBU_OP_UTF16LE_TO_UTF8 = 1,           /* as gbu_utf16le_to_utf8            */
     GBU_OP_UTF16_LENGTH_FROM_UTF8 = 2,    /* as gbu_utf16_length_from_utf8     */
-    GBU_OP_UTF8_LENGTH_FROM_UTF16LE = 3   /* as gbu_utf8_length_from_utf16le   */
+    GBU_OP_UTF8_LENGTH_FROM_UTF16LE = 3,  /* as gbu_utf8_length_from_utf16le   */
+    GBU_OP_UTF8_TO_UTF16BE = 4,           /* as gbu_utf8_to_utf16be            */
+    GBU_OP_UTF16BE_TO_UTF8 = 5,           /* as gbu_utf16be_to_utf8            */
+    GBU_OP_UTF8_LENGTH_FROM_UTF16BE = 6   /* as gbu_utf8_length_from_utf16be   */
 } gbu_op;
 
 typedef struct gbu_batch_item {

@@ -143,5 +143,29 @@ def utf8_length_from_utf16le(data) -> Result:
     return Result(r.status, r.in_offset, r.out_len)
 
 
+# UTF-16BE (Sec. 2.1: the same words with the high byte first): the UTF-16LE
+# oracle applied to byte-swapped words, which is the definition of the order.
+def _swap_words(data) -> np.ndarray:
+    src = _as_u8(data)
+    if src.size % 2:
+        raise ValueError("UTF-16 input must have an even number of bytes")
+    return src.reshape(-1, 2)[:, ::-1].reshape(-1).copy()
+
+
+def utf8_to_utf16be(data, cap_units: int | None = None):
+    """Transcode UTF-8 bytes to UTF-16BE; returns (Result, big-endian bytes)."""
+    res, out = utf8_to_utf16le(data, cap_units)
+    return res, _swap_words(out.view(np.uint8))
+
+
+def utf16be_to_utf8(data, cap_bytes: int | None = None):
+    """Transcode UTF-16BE bytes; returns (Result, uint8 array)."""
+    return utf16le_to_utf8(_swap_words(data), cap_bytes)
+
+
+def utf8_length_from_utf16be(data) -> Result:
+    return utf8_length_from_utf16le(_swap_words(data))
+
+
 def library_path() -> str:
     return os.path.abspath(_build.build())

@@ -56,6 +56,9 @@ GBU_OP_UTF8_TO_UTF16LE = 0
 GBU_OP_UTF16LE_TO_UTF8 = 1
 GBU_OP_UTF16_LENGTH_FROM_UTF8 = 2
 GBU_OP_UTF8_LENGTH_FROM_UTF16LE = 3
+GBU_OP_UTF8_TO_UTF16BE = 4
+GBU_OP_UTF16BE_TO_UTF8 = 5
+GBU_OP_UTF8_LENGTH_FROM_UTF16BE = 6
 
 
 class gbu_batch_item(ctypes.Structure):
@@ -97,6 +100,12 @@ SIGNATURES = {
     "gbu_utf16le_to_utf8": (gbu_result, [_VP, _VP, _U64, _VP, _U64, _VP]),
     "gbu_utf16_length_from_utf8": (gbu_result, [_VP, _VP, _U64, _VP]),
     "gbu_utf8_length_from_utf16le": (gbu_result, [_VP, _VP, _U64, _VP]),
+    "gbu_utf8_to_utf16be": (gbu_result, [_VP, _VP, _U64, _VP, _U64, _VP]),
+    "gbu_utf16be_to_utf8": (gbu_result, [_VP, _VP, _U64, _VP, _U64, _VP]),
+    "gbu_utf8_length_from_utf16be": (gbu_result, [_VP, _VP, _U64, _VP]),
+    "gbu_validate_utf16be": (gbu_result, [_VP, _VP, _U64, _VP]),
+    "gbu_utf8_to_utf16be_async": (_I32, [_VP, _VP, _U64, _VP, _U64, _VP, _VP]),
+    "gbu_utf16be_to_utf8_async": (_I32, [_VP, _VP, _U64, _VP, _U64, _VP, _VP]),
     "gbu_validate_utf8": (gbu_result, [_VP, _VP, _U64, _VP]),
     "gbu_validate_utf16le": (gbu_result, [_VP, _VP, _U64, _VP]),
     "gbu_validate_utf8_async": (_I32, [_VP, _VP, _U64, _VP, _VP]),
@@ -184,6 +193,30 @@ def gbu_utf16_length_from_utf8(ctx, d_in, n_bytes, stream=0) -> Result:
 
 def gbu_utf8_length_from_utf16le(ctx, d_in, n_units, stream=0) -> Result:
     return _res(load().gbu_utf8_length_from_utf16le(ctx, d_in, n_units, stream))
+
+
+def gbu_utf8_to_utf16be(ctx, d_in, n_bytes, d_out, cap_units, stream=0) -> Result:
+    return _res(load().gbu_utf8_to_utf16be(ctx, d_in, n_bytes, d_out, cap_units, stream))
+
+
+def gbu_utf16be_to_utf8(ctx, d_in, n_units, d_out, cap_bytes, stream=0) -> Result:
+    return _res(load().gbu_utf16be_to_utf8(ctx, d_in, n_units, d_out, cap_bytes, stream))
+
+
+def gbu_utf8_length_from_utf16be(ctx, d_in, n_units, stream=0) -> Result:
+    return _res(load().gbu_utf8_length_from_utf16be(ctx, d_in, n_units, stream))
+
+
+def gbu_validate_utf16be(ctx, d_in, n_units, stream=0) -> Result:
+    return _res(load().gbu_validate_utf16be(ctx, d_in, n_units, stream))
+
+
+def gbu_utf8_to_utf16be_async(ctx, d_in, n_bytes, d_out, cap_units, d_result, stream=0) -> int:
+    return load().gbu_utf8_to_utf16be_async(ctx, d_in, n_bytes, d_out, cap_units, d_result, stream)
+
+
+def gbu_utf16be_to_utf8_async(ctx, d_in, n_units, d_out, cap_bytes, d_result, stream=0) -> int:
+    return load().gbu_utf16be_to_utf8_async(ctx, d_in, n_units, d_out, cap_bytes, d_result, stream)
 
 
 def gbu_validate_utf8(ctx, d_in, n_bytes, stream=0) -> Result:

@@ -66,6 +66,23 @@ namespace {
 
 bool ok(cudaError_t e) { return e == cudaSuccess; }
 
+// Properties of a gbu_op.
+bool op_utf16_in(int32_t op)
+{
+    return op == GBU_OP_UTF16LE_TO_UTF8 || op == GBU_OP_UTF8_LENGTH_FROM_UTF16LE ||
+           op == GBU_OP_UTF16BE_TO_UTF8 || op == GBU_OP_UTF8_LENGTH_FROM_UTF16BE;
+}
+bool op_writes(int32_t op)
+{
+    return op == GBU_OP_UTF8_TO_UTF16LE || op == GBU_OP_UTF16LE_TO_UTF8 ||
+           op == GBU_OP_UTF8_TO_UTF16BE || op == GBU_OP_UTF16BE_TO_UTF8;
+}
+bool op_big_endian(int32_t op)
+{
+    return op == GBU_OP_UTF8_TO_UTF16BE || op == GBU_OP_UTF16BE_TO_UTF8 ||
+           op == GBU_OP_UTF8_LENGTH_FROM_UTF16BE;
+}
+
 // Point a one-item job at the context's scratch.
 void attach_scratch(gbu_ctx *c, Job &J)
 {
@@ -113,7 +130,9 @@ int32_t ensure_scratch(gbu_ctx *c, uint64_t chunks, cudaStream_t stream)
     return GBU_OK;
 }
 
-enum class Op { U8toU16, U16toU8 };
+enum class Op { U8toU16, U16toU8, U8toU16BE, U16BEtoU8 };
+bool utf16_in(Op op) { return op == Op::U16toU8 || op == Op::U16BEtoU8; }
+bool big_endian(Op op) { return op == Op::U8toU16BE || op == Op::U16BEtoU8; }
 
 // Enqueue one call; result goes to `dst` (device-visible). `validate`: the
 // validation-only form (implies !write).
@@ -122,16 +141,16 @@ int32_t enqueue(gbu_ctx *c, Op op, const void *in, uint64_t n, void *out, uint64
 {
     if (!c || !dst || (n && !in) || (write && cap && !out)) return GBU_INVALID_ARG;
     if (n >= kMaxUnits) return GBU_INVALID_ARG;
-    if (op == Op::U16toU8 && (reinterpret_cast<uintptr_t>(in) & 1u)) return GBU_INVALID_ARG;
-    if (op == Op::U8toU16 && write && (reinterpret_cast<uintptr_t>(out) & 1u)) return GBU_INVALID_ARG;
+    if (utf16_in(op) && (reinterpret_cast<uintptr_t>(in) & 1u)) return GBU_INVALID_ARG;
+    if (!utf16_in(op) && write && (reinterpret_cast<uintptr_t>(out) & 1u)) return GBU_INVALID_ARG;
     if (!ok(cudaSetDevice(c->device))) return GBU_DEVICE_ERROR;
     if (n == 0) {
         g_launches.fetch_add(1, std::memory_order_relaxed);
         return ok(launch_write_result(dst, GBU_OK, 0, 0, stream)) ? GBU_OK : GBU_DEVICE_ERROR;
     }
-    const bool utf16 = op == Op::U16toU8;
+    const bool utf16 = utf16_in(op);
     Job J{};
-    J.item0 = make_item(in, n, utf16, out, cap, write, dst, 0);
+    J.item0 = make_item(in, n, utf16, out, cap, write, dst, 0, big_endian(op));
     J.num_items = 1;
     J.total_chunks = J.item0.nchunks;
     J.validate = validate ? 1u : 0u;
@@ -269,6 +288,43 @@ int32_t gbu_validate_utf16le_async(gbu_ctx *c, const uint16_t *d_in, uint64_t n,
                    reinterpret_cast<ResultSlot *>(d_result), static_cast<cudaStream_t>(stream), true);
 }
 
+gbu_result gbu_utf8_to_utf16be(gbu_ctx *c, const uint8_t *d_in, uint64_t n, uint16_t *d_out,
+                               uint64_t cap, void *stream)
+{
+    return run_sync(c, Op::U8toU16BE, d_in, n, d_out, cap, true, stream);
+}
+
+gbu_result gbu_utf16be_to_utf8(gbu_ctx *c, const uint16_t *d_in, uint64_t n, uint8_t *d_out,
+                               uint64_t cap, void *stream)
+{
+    return run_sync(c, Op::U16BEtoU8, d_in, n, d_out, cap, true, stream);
+}
+
+gbu_result gbu_utf8_length_from_utf16be(gbu_ctx *c, const uint16_t *d_in, uint64_t n,
+                                        void *stream)
+{
+    return run_sync(c, Op::U16BEtoU8, d_in, n, nullptr, 0, false, stream);
+}
+
+gbu_result gbu_validate_utf16be(gbu_ctx *c, const uint16_t *d_in, uint64_t n, void *stream)
+{
+    return run_sync(c, Op::U16BEtoU8, d_in, n, nullptr, 0, false, stream, true);
+}
+
+int32_t gbu_utf8_to_utf16be_async(gbu_ctx *c, const uint8_t *d_in, uint64_t n, uint16_t *d_out,
+                                  uint64_t cap, gbu_result *result, void *stream)
+{
+    return enqueue(c, Op::U8toU16BE, d_in, n, d_out, cap, true,
+                   reinterpret_cast<ResultSlot *>(result), static_cast<cudaStream_t>(stream));
+}
+
+int32_t gbu_utf16be_to_utf8_async(gbu_ctx *c, const uint16_t *d_in, uint64_t n, uint8_t *d_out,
+                                  uint64_t cap, gbu_result *result, void *stream)
+{
+    return enqueue(c, Op::U16BEtoU8, d_in, n, d_out, cap, true,
+                   reinterpret_cast<ResultSlot *>(result), static_cast<cudaStream_t>(stream));
+}
+
 gbu_result gbu_utf8_length_from_utf16le(gbu_ctx *c, const uint16_t *d_in, uint64_t n,
                                         void *stream)
 {
@@ -311,8 +367,8 @@ static gbu_result run_host(gbu_ctx *c, Op op, const void *h_in, uint64_t n, void
     if (n >= kMaxUnits) return make(GBU_INVALID_ARG);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (!ok(cudaSetDevice(c->device))) return make(GBU_DEVICE_ERROR);
-    const size_t in_bytes = op == Op::U8toU16 ? n : 2 * n;
-    const size_t ub = op == Op::U8toU16 ? 2 : 1;
+    const size_t in_bytes = utf16_in(op) ? 2 * n : n;
+    const size_t ub = utf16_in(op) ? 1 : 2;
     const size_t in_al = (in_bytes + 255) & ~size_t(255);
     const size_t need = in_al + cap * ub + 16;
     if (need > c->io_bytes) {
@@ -394,10 +450,10 @@ int32_t gbu_batch_plan(gbu_ctx *c, const gbu_batch_item *items, uint32_t count,
     bool any_write = false;
     for (uint32_t i = 0; i < count; i++) {
         const gbu_batch_item &b = items[i];
-        if (b.op < GBU_OP_UTF8_TO_UTF16LE || b.op > GBU_OP_UTF8_LENGTH_FROM_UTF16LE)
+        if (b.op < GBU_OP_UTF8_TO_UTF16LE || b.op > GBU_OP_UTF8_LENGTH_FROM_UTF16BE)
             return GBU_INVALID_ARG;
-        const bool utf16 = b.op == GBU_OP_UTF16LE_TO_UTF8 || b.op == GBU_OP_UTF8_LENGTH_FROM_UTF16LE;
-        const bool write = b.op <= GBU_OP_UTF16LE_TO_UTF8;
+        const bool utf16 = op_utf16_in(b.op);
+        const bool write = op_writes(b.op);
         if (b.n >= kMaxUnits || (b.n && !b.in)) return GBU_INVALID_ARG;
         if (utf16 && (reinterpret_cast<uintptr_t>(b.in) & 1u)) return GBU_INVALID_ARG;
         if (write && b.cap && !b.out) return GBU_INVALID_ARG;
@@ -416,14 +472,13 @@ int32_t gbu_batch_plan(gbu_ctx *c, const gbu_batch_item *items, uint32_t count,
     // result slot): a CTA then mostly runs one code path at a time, which
     // keeps the instruction cache warm.
     uint32_t base = 0;
-    for (int op = GBU_OP_UTF8_TO_UTF16LE; op <= GBU_OP_UTF8_LENGTH_FROM_UTF16LE; op++) {
+    for (int op = GBU_OP_UTF8_TO_UTF16LE; op <= GBU_OP_UTF8_LENGTH_FROM_UTF16BE; op++) {
         for (uint32_t i = 0; i < count; i++) {
             const gbu_batch_item &b = items[i];
             if (b.op != op) continue;
-            const bool utf16 = b.op == GBU_OP_UTF16LE_TO_UTF8 || b.op == GBU_OP_UTF8_LENGTH_FROM_UTF16LE;
-            const bool write = b.op <= GBU_OP_UTF16LE_TO_UTF8;
-            Item I = make_item(b.in, b.n, utf16, b.out, b.cap, write,
-                               reinterpret_cast<ResultSlot *>(results + i), base);
+            Item I = make_item(b.in, b.n, op_utf16_in(b.op), b.out, b.cap, op_writes(b.op),
+                               reinterpret_cast<ResultSlot *>(results + i), base,
+                               op_big_endian(b.op));
             c->h_items[i] = I;
             for (uint32_t k = 0; k < I.nchunks; k++) c->h_chunk_item[base + k] = i;
             base += I.nchunks;

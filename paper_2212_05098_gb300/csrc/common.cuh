@@ -92,7 +92,9 @@ struct ResultSlot {      // layout of gbu_result
 };
 
 // One input of a job.
-enum : uint32_t { kOpUtf16 = 1u, kOpWrite = 2u };   // bit 0: input is UTF-16; bit 1: write output
+// bit 0: input is UTF-16 (else UTF-8); bit 1: write output; bit 2: the UTF-16
+// side (input or output) is big-endian
+enum : uint32_t { kOpUtf16 = 1u, kOpWrite = 2u, kOpBE = 4u };
 struct __align__(16) Item {   // 64 bytes, copied into shared memory in 16-byte pieces
     const uint8_t *in_al;   // 16-byte aligned base at or before the input
     uint8_t *out;           // output (UTF-16 words or UTF-8 bytes)

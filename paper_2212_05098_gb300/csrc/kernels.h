@@ -23,7 +23,7 @@ constexpr size_t kHeaderBytes = 256;
 
 // Describe one input (chunk count included) for a job starting at chunk_base.
 Item make_item(const void *in, uint64_t n, bool utf16, void *out, uint64_t cap, bool write,
-               ResultSlot *result, uint32_t chunk_base);
+               ResultSlot *result, uint32_t chunk_base, bool big_endian = false);
 
 // Tuning parameters of a launch: look-back width (status words per lane per
 // round, one of kLookWidths) and resident CTAs per SM (0: as many as fit).

@@ -93,14 +93,17 @@ uint64_t round_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
 
 bool is_utf16_op(int32_t op)
 {
-    return op == GBU_OP_UTF16LE_TO_UTF8 || op == GBU_OP_UTF8_LENGTH_FROM_UTF16LE;
+    return op == GBU_OP_UTF16LE_TO_UTF8 || op == GBU_OP_UTF8_LENGTH_FROM_UTF16LE ||
+           op == GBU_OP_UTF16BE_TO_UTF8 || op == GBU_OP_UTF8_LENGTH_FROM_UTF16BE;
 }
 
 // Worst-case output bytes of a request (the capacity it is given).
 uint64_t out_bytes(const gbu_request &r)
 {
-    if (r.op == GBU_OP_UTF8_TO_UTF16LE) return 2 * r.n;   // one unit per byte
-    if (r.op == GBU_OP_UTF16LE_TO_UTF8) return 3 * r.n;   // three bytes per unit
+    if (r.op == GBU_OP_UTF8_TO_UTF16LE || r.op == GBU_OP_UTF8_TO_UTF16BE)
+        return 2 * r.n;   // one unit per byte
+    if (r.op == GBU_OP_UTF16LE_TO_UTF8 || r.op == GBU_OP_UTF16BE_TO_UTF8)
+        return 3 * r.n;   // three bytes per unit
     return 0;
 }
 
@@ -210,9 +213,10 @@ bool gbu_server::launch(Slot &s)
         it.n = p.req.n;
         it.op = p.req.op;
         it.reserved = 0;
-        const bool write = p.req.op == GBU_OP_UTF8_TO_UTF16LE || p.req.op == GBU_OP_UTF16LE_TO_UTF8;
+        const bool write = p.req.op == GBU_OP_UTF8_TO_UTF16LE || p.req.op == GBU_OP_UTF16LE_TO_UTF8 ||
+                           p.req.op == GBU_OP_UTF8_TO_UTF16BE || p.req.op == GBU_OP_UTF16BE_TO_UTF8;
         it.out = write ? out : nullptr;
-        it.cap = write ? (p.req.op == GBU_OP_UTF8_TO_UTF16LE ? p.req.n : 3 * p.req.n) : 0;
+        it.cap = write ? (is_utf16_op(p.req.op) ? 3 * p.req.n : p.req.n) : 0;
     }
     if (gbu_batch_plan(s.ctx, s.items.data(), n, s.d_res, s.stream) != GBU_OK) return false;
     if (!ok(cudaMemcpyAsync(s.d_seg, s.h_seg, n * sizeof(Seg), cudaMemcpyHostToDevice, s.stream)))
@@ -372,7 +376,7 @@ int32_t gbu_server_submit(gbu_server *srv, const gbu_request *req)
 {
     if (!srv || !req) return GBU_INVALID_ARG;
     const gbu_request &r = *req;
-    if (r.op < GBU_OP_UTF8_TO_UTF16LE || r.op > GBU_OP_UTF8_LENGTH_FROM_UTF16LE) return GBU_INVALID_ARG;
+    if (r.op < GBU_OP_UTF8_TO_UTF16LE || r.op > GBU_OP_UTF8_LENGTH_FROM_UTF16BE) return GBU_INVALID_ARG;
     if (r.n && !r.in) return GBU_INVALID_ARG;
     if (is_utf16_op(r.op) && (reinterpret_cast<uintptr_t>(r.in) & 1u)) return GBU_INVALID_ARG;
     if (block_bytes(r) > srv->pool.size()) return GBU_INVALID_ARG;   // could never be admitted
@@ -411,7 +415,7 @@ int32_t gbu_server_replay(gbu_server *srv, const gbu_request *reqs, const double
     if (!srv || (count && (!reqs || !t_arrival || !out))) return GBU_INVALID_ARG;
     for (uint32_t i = 0; i < count; i++) {
         gbu_request r = reqs[i];
-        if (r.op < GBU_OP_UTF8_TO_UTF16LE || r.op > GBU_OP_UTF8_LENGTH_FROM_UTF16LE ||
+        if (r.op < GBU_OP_UTF8_TO_UTF16LE || r.op > GBU_OP_UTF8_LENGTH_FROM_UTF16BE ||
             (r.n && !r.in) || block_bytes(r) > srv->pool.size() ||
             (is_utf16_op(r.op) && (reinterpret_cast<uintptr_t>(r.in) & 1u)))
             return GBU_INVALID_ARG;

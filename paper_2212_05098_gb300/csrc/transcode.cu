@@ -278,7 +278,7 @@ __device__ __forceinline__ uint32_t chunk8_phase1(St8 &st, const uint8_t *stage,
 template <bool kWrite>
 __device__ __forceinline__ void chunk8_phase2(St8 &st, const uint8_t *stage, uint8_t *obuf,
                                               uint32_t t_off, int64_t vt, int64_t lo, int64_t hi,
-                                              unsigned long long *s_err)
+                                              unsigned long long *s_err, bool be)
 {
     if (st.skip) return;
     // Threads straddling an end of the input see the bytes outside it as
@@ -324,6 +324,10 @@ __device__ __forceinline__ void chunk8_phase2(St8 &st, const uint8_t *stage, uin
             const uint32_t hb = ((wb >> 4) & 0x0FFF0FFFu) + 0xD7C0D7C0u;
             wa = ((ha & hma) | (wa & ~hma)) | (lma & 0xDC00DC00u);
             wb = ((hb & hmb) | (wb & ~hmb)) | (lmb & 0xDC00DC00u);
+        }
+        if (be) {   // UTF-16BE output
+            wa = prmt(wa, 0, 0x2301);
+            wb = prmt(wb, 0, 0x2301);
         }
         const uint32_t e = st.end[j - 1];
         if (e & 0x00000080u) *p++ = (uint16_t)wa;
@@ -397,7 +401,7 @@ __device__ __forceinline__ uint32_t unit_keep(int64_t u, int64_t lo, int64_t hi)
 }
 
 __device__ __forceinline__ uint32_t chunk16_phase1(St16 &st, const uint8_t *stage, int64_t vt,
-                                                   int64_t lo, int64_t hi)
+                                                   int64_t lo, int64_t hi, bool be)
 {
     const uint8_t *sp = stage + kHalo + 32 * threadIdx.x;
     const uint4 a = *reinterpret_cast<const uint4 *>(sp);
@@ -437,6 +441,10 @@ __device__ __forceinline__ uint32_t chunk16_phase1(St16 &st, const uint8_t *stag
     if (!outside && (vt - 2 < lo || vt + 18 > hi)) {
         w[0] &= unit_keep(vt - 2, lo, hi) | (unit_keep(vt - 1, lo, hi) << 16);
         w[9] &= unit_keep(vt + 16, lo, hi) | (unit_keep(vt + 17, lo, hi) << 16);
+    }
+    if (be) {   // UTF-16BE: swap the bytes of every word once, then as UTF-16LE
+#pragma unroll
+        for (int j = 0; j < 10; j++) w[j] = prmt(w[j], 0, 0x2301);
     }
     uint32_t cnt = 0, any800 = 0, anysur = 0;
 #pragma unroll
@@ -894,7 +902,7 @@ transcode_kernel(const Job J)
         if (I.op & kOpUtf16) {
             const int64_t vt = (int64_t)k * kChunk16 + 16 * tid;
             St16 st;
-            const uint32_t cnt = chunk16_phase1(st, stage, vt, lo, hi);
+            const uint32_t cnt = chunk16_phase1(st, stage, vt, lo, hi, (I.op & kOpBE) != 0);
             t_off = block_exclusive_scan(cnt, s_warp, &agg);
             hand_over();
             if (iter >= kDepth && cw_sync_or(!write_out(iter - kDepth))) {
@@ -912,7 +920,7 @@ transcode_kernel(const Job J)
                 failed = true;
                 break;
             }
-            chunk8_phase2<kWrite>(st, stage, obuf, t_off, vt, lo, hi, &s_err[p]);
+            chunk8_phase2<kWrite>(st, stage, obuf, t_off, vt, lo, hi, &s_err[p], (I.op & kOpBE) != 0);
         }
         // every thread read this iteration's R.item[slot] at its start: the
         // slot's descriptor can be replaced by the one the next load needs
@@ -1017,7 +1025,7 @@ cudaError_t launch_write_result(ResultSlot *dst, int32_t status, uint64_t in_off
 }
 
 Item make_item(const void *in, uint64_t n, bool utf16, void *out, uint64_t cap, bool write,
-               ResultSlot *result, uint32_t chunk_base)
+               ResultSlot *result, uint32_t chunk_base, bool big_endian)
 {
     Item I{};
     const uintptr_t p = reinterpret_cast<uintptr_t>(in);
@@ -1032,7 +1040,7 @@ Item make_item(const void *in, uint64_t n, bool utf16, void *out, uint64_t cap, 
     I.out = static_cast<uint8_t *>(out);
     I.cap = write ? cap : 0;
     I.result = result;
-    I.op = (utf16 ? kOpUtf16 : 0u) | (write ? kOpWrite : 0u);
+    I.op = (utf16 ? kOpUtf16 : 0u) | (write ? kOpWrite : 0u) | (big_endian ? kOpBE : 0u);
     I.chunk_base = chunk_base;
     const uint64_t units = utf16 ? kChunk16 : kChunk8;
     const uint64_t nch = n ? (I.head + n + units - 1) / units : 1;

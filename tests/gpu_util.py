@@ -24,7 +24,7 @@ class DevIn:
         data = np.ascontiguousarray(data, dtype=np.uint8)
         self.buf = t.zeros(data.size + off + 32, dtype=t.uint8, device="cuda")
         if data.size:
-            self.buf[off:off + data.size] = t.from_numpy(data).cuda()
+            self.buf[off:off + data.size] = t.from_numpy(np.array(data, copy=True)).cuda()
         self.ptr = self.buf.data_ptr() + off
         self.nbytes = data.size
 
@@ -116,4 +116,41 @@ def check_u16(ctx, data: np.ndarray, cap_bytes=None, in_off=0, out_off=0):
     assert triple(lr) == triple(lref), (triple(lr), triple(lref))
     vr = gbu.gbu_validate_utf16le(ctx, din.ptr, data.size // 2, 0)
     assert triple(vr) == (lref.status, lref.in_offset, 0), (triple(vr), triple(lref))
+    return r
+
+
+def check_u8_be(ctx, data: np.ndarray, cap_units=None, in_off=0, out_off=0):
+    """UTF-8 -> UTF-16BE on the GPU vs the oracle."""
+    data = np.ascontiguousarray(data, dtype=np.uint8)
+    ref, ref_out = oracle.utf8_to_utf16be(data, cap_units)
+    din = DevIn(data, in_off)
+    cap = data.size if cap_units is None else cap_units
+    dout = DevOut(2 * cap, out_off)
+    r = gbu.gbu_utf8_to_utf16be(ctx, din.ptr, data.size, dout.ptr, cap, 0)
+    assert triple(r) == triple(ref), (triple(r), triple(ref))
+    keep = min(ref.out_len, cap)
+    assert np.array_equal(dout.data(2 * keep), ref_out[: 2 * keep])
+    assert dout.guards_intact(), "write outside [0, cap)"
+    return r
+
+
+def check_u16_be(ctx, data: np.ndarray, cap_bytes=None, in_off=0, out_off=0):
+    """UTF-16BE (bytes, high byte first) -> UTF-8 on the GPU vs the oracle,
+    plus the BE length and validation calls."""
+    data = np.ascontiguousarray(data, dtype=np.uint8)
+    ref, ref_out = oracle.utf16be_to_utf8(data, cap_bytes)
+    din = DevIn(data, in_off)
+    n = data.size // 2
+    cap = 3 * n if cap_bytes is None else cap_bytes
+    dout = DevOut(cap, out_off)
+    r = gbu.gbu_utf16be_to_utf8(ctx, din.ptr, n, dout.ptr, cap, 0)
+    assert triple(r) == triple(ref), (triple(r), triple(ref))
+    keep = min(ref.out_len, cap)
+    assert np.array_equal(dout.data(keep), ref_out[:keep])
+    assert dout.guards_intact(), "write outside [0, cap)"
+    lr = gbu.gbu_utf8_length_from_utf16be(ctx, din.ptr, n, 0)
+    lref = oracle.utf8_length_from_utf16be(data)
+    assert triple(lr) == triple(lref)
+    vr = gbu.gbu_validate_utf16be(ctx, din.ptr, n, 0)
+    assert triple(vr) == (lref.status, lref.in_offset, 0)
     return r

@@ -274,3 +274,48 @@ def test_autotune_and_cache(ctx, tmp_path):
         _run(ctx, b, gbu.gbu_batch_launch_graph)
     finally:
         assert gbu.gbu_set_tune(ctx, 4, 0) == gbu.GBU_OK
+
+
+def test_batch_big_endian_ops(ctx):
+    """UTF-16BE operations in a batch next to UTF-16LE ones."""
+    import torch
+    rng = np.random.default_rng(90)
+    items, checks, keep = [], [], []
+    res = torch.zeros(24 * 12, dtype=torch.uint8, device="cuda")
+    for i in range(12):
+        prof = list(textgen.PROFILES)[i % 5]
+        t8 = textgen.generate(prof, 50_000 + 977 * i, textgen.UTF8, seed=900 + i).data
+        t16 = textgen.generate(prof, 2 * (40_000 + 313 * i), textgen.UTF16, seed=950 + i).data
+        be16 = t16.reshape(-1, 2)[:, ::-1].reshape(-1).copy()
+        if i % 4 == 3:
+            be16.view(">u2")[777] = 0xD801                  # lone high
+        op = [gbu.GBU_OP_UTF8_TO_UTF16BE, gbu.GBU_OP_UTF16BE_TO_UTF8,
+              gbu.GBU_OP_UTF8_LENGTH_FROM_UTF16BE, gbu.GBU_OP_UTF8_TO_UTF16LE][i % 4]
+        src = t8 if op in (gbu.GBU_OP_UTF8_TO_UTF16BE, gbu.GBU_OP_UTF8_TO_UTF16LE) else be16
+        d_in = torch.from_numpy(src).cuda()
+        n = src.size if src is t8 else src.size // 2
+        cap = n if src is t8 else 3 * n
+        d_out = torch.full((2 * cap + 64,), 0xA5, dtype=torch.uint8, device="cuda")
+        keep += [d_in, d_out]
+        writes = op != gbu.GBU_OP_UTF8_LENGTH_FROM_UTF16BE
+        items.append((d_in.data_ptr(), n, d_out.data_ptr() if writes else 0, cap if writes else 0, op))
+        checks.append((op, src, d_out, cap))
+    assert gbu.gbu_batch_plan(ctx, items, res.data_ptr(), 0) == gbu.GBU_OK
+    for launch in (gbu.gbu_batch_launch, gbu.gbu_batch_launch_graph):
+        assert launch(ctx, 0) == gbu.GBU_OK
+        torch.cuda.synchronize()
+        got = np.frombuffer(res.cpu().numpy().tobytes(), dtype=RESULT_DTYPE)
+        for i, (op, src, d_out, cap) in enumerate(checks):
+            if op == gbu.GBU_OP_UTF8_TO_UTF16BE:
+                ref, out = oracle.utf8_to_utf16be(src, cap)
+            elif op == gbu.GBU_OP_UTF16BE_TO_UTF8:
+                ref, out = oracle.utf16be_to_utf8(src, cap)
+            elif op == gbu.GBU_OP_UTF8_LENGTH_FROM_UTF16BE:
+                ref, out = oracle.utf8_length_from_utf16be(src), None
+            else:
+                ref, out = oracle.utf8_to_utf16le(src, cap)
+                out = out.view(np.uint8)
+            assert (int(got[i]["status"]), int(got[i]["in_offset"]), int(got[i]["out_len"])) == \
+                (ref.status, ref.in_offset, ref.out_len), i
+            if out is not None:
+                assert np.array_equal(d_out[: out.size].cpu().numpy(), out), i

@@ -255,3 +255,25 @@ def test_encoding_error_takes_precedence_over_capacity():
     r, part = oracle.utf16le_to_utf8(_u16([0x41, 0x4E00, 0xDC00]), cap_bytes=2)
     assert r == oracle.Result(oracle.LONE_LOW_SURROGATE, 2, 4)
     assert part.tobytes() == bytes([0x41, 0xE4])
+
+
+def test_utf16be_matches_python_codecs():
+    """UTF-16BE forms against Python's own big-endian codec on every profile,
+    and errors at the same units as in UTF-16LE."""
+    import textgen
+    for prof in textgen.PROFILES:
+        t = textgen.generate(prof, 20_000, textgen.UTF8, seed=7)
+        text = t.data.tobytes().decode("utf-8")
+        be = text.encode("utf-16-be")
+        r, out = oracle.utf8_to_utf16be(t.data)
+        assert r.status == oracle.OK and out.tobytes() == be
+        r2, back = oracle.utf16be_to_utf8(np.frombuffer(be, np.uint8))
+        assert r2.status == oracle.OK and back.tobytes() == t.data.tobytes()
+        assert oracle.utf8_length_from_utf16be(np.frombuffer(be, np.uint8)).out_len == len(t.data)
+    # a lone high surrogate: same kind and unit offset in both byte orders
+    le = np.array([0x41, 0xD800, 0x42], dtype="<u2")
+    be = le.astype(">u2").view(np.uint8)
+    ra, _ = oracle.utf16le_to_utf8(le.view(np.uint8))
+    rb, _ = oracle.utf16be_to_utf8(be)
+    assert (ra.status, ra.in_offset, ra.out_len) == (rb.status, rb.in_offset, rb.out_len)
+    assert rb.status == oracle.LONE_HIGH_SURROGATE and rb.in_offset == 1

@@ -201,3 +201,24 @@ def test_injected_errors_at_chunk_edges(ctx, enc):
         data = p.apply(text.data)
         r = check_u8(ctx, data) if enc == textgen.UTF8 else check_u16(ctx, data)
         assert triple(r) == (p.kind, p.err_unit, p.prefix_out), p.case
+
+
+@pytest.mark.parametrize("profile", list(textgen.PROFILES))
+def test_utf16be_both_directions(ctx, profile):
+    """UTF-16BE forms: ragged sizes, both directions, corrupted copies."""
+    from gpu_util import check_u16_be, check_u8_be
+    big8 = textgen.generate(profile, 3 * 8192 + 200, textgen.UTF8, seed=61)
+    t16 = textgen.generate(profile, 2 * (3 * 8192 + 200), textgen.UTF16, seed=62)
+    be16 = t16.data.reshape(-1, 2)[:, ::-1].reshape(-1).copy()
+    for n in (1, 2, 17, 4095, 4096, 4097, 8193, 3 * 8192 + 101):
+        check_u8_be(ctx, big8.data[:n])
+        check_u16_be(ctx, be16[: 2 * n])
+    check_u8_be(ctx, big8.data, in_off=3, out_off=6)
+    check_u16_be(ctx, be16, in_off=2, out_off=5)
+    for k in range(4):
+        check_u8_be(ctx, textgen.mutate(big8.data, 2, seed=63 + k))
+        bad = be16.copy().view(">u2")
+        bad[1000 + 3000 * k] = 0xDC00 + k      # lone low surrogate
+        check_u16_be(ctx, bad.view(np.uint8))
+    check_u8_be(ctx, big8.data, cap_units=100)
+    check_u16_be(ctx, be16, cap_bytes=333)

@@ -60,6 +60,10 @@ struct gbu_ctx {
     cudaStream_t capture_stream = nullptr;
     cudaGraphExec_t graph = nullptr;
     gbu::Tune tune;                   // launch parameters of every call on the context
+    // host-buffer pipeline: copy streams, per-slice events and mapped results
+    cudaStream_t h2d = nullptr, d2h = nullptr;
+    cudaEvent_t ev_in[64] = {}, ev_done[64] = {};
+    gbu_result *h_slice_res = nullptr, *d_slice_res = nullptr;
 };
 
 namespace {
@@ -233,6 +237,13 @@ void gbu_destroy(gbu_ctx *c)
     if (c->d_item_done) cudaFree(c->d_item_done);
     if (c->scratch) cudaFree(c->scratch);
     if (c->io) cudaFree(c->io);
+    for (int k = 0; k < 64; k++) {
+        if (c->ev_in[k]) cudaEventDestroy(c->ev_in[k]);
+        if (c->ev_done[k]) cudaEventDestroy(c->ev_done[k]);
+    }
+    if (c->h2d) cudaStreamDestroy(c->h2d);
+    if (c->d2h) cudaStreamDestroy(c->d2h);
+    if (c->h_slice_res) cudaFreeHost(c->h_slice_res);
     if (c->h_result) cudaFreeHost(c->h_result);
     delete c;
 }
@@ -359,6 +370,38 @@ int32_t gbu_utf8_length_from_utf16le_async(gbu_ctx *c, const uint16_t *d_in, uin
                    reinterpret_cast<ResultSlot *>(result), static_cast<cudaStream_t>(stream));
 }
 
+// Host-buffer form. Inputs of a few slices or more are cut at character
+// boundaries into slices that are copied in, transcoded and copied out in a
+// pipeline (copy-in on one stream, kernels on the caller's stream, copy-out
+// on a third), so both copy directions and the kernels overlap. Each slice is
+// an independent call; the results are joined on the host in order: the
+// first slice with an encoding error ends the input (offset and valid prefix
+// shifted by the slices before it), and a total above the capacity is
+// OUTPUT_TOO_SMALL with the required length, as for the one-call form.
+static constexpr int kMaxSlices = 64;
+static constexpr uint64_t kMinSliceBytes = 32ull << 20;
+
+static bool host_pipeline_ready(gbu_ctx *c)
+{
+    if (!c->h2d && !ok(cudaStreamCreateWithFlags(&c->h2d, cudaStreamNonBlocking))) return false;
+    if (!c->d2h && !ok(cudaStreamCreateWithFlags(&c->d2h, cudaStreamNonBlocking))) return false;
+    for (int k = 0; k < kMaxSlices; k++) {
+        if (!c->ev_in[k] && !ok(cudaEventCreateWithFlags(&c->ev_in[k], cudaEventDisableTiming)))
+            return false;
+        if (!c->ev_done[k] && !ok(cudaEventCreateWithFlags(&c->ev_done[k], cudaEventDisableTiming)))
+            return false;
+    }
+    if (!c->h_slice_res) {
+        void *h = nullptr, *d = nullptr;
+        if (!ok(cudaHostAlloc(&h, kMaxSlices * sizeof(gbu_result), cudaHostAllocMapped)) ||
+            !ok(cudaHostGetDevicePointer(&d, h, 0)))
+            return false;
+        c->h_slice_res = static_cast<gbu_result *>(h);
+        c->d_slice_res = static_cast<gbu_result *>(d);
+    }
+    return true;
+}
+
 static gbu_result run_host(gbu_ctx *c, Op op, const void *h_in, uint64_t n, void *h_out,
                            uint64_t cap, void *stream)
 {
@@ -367,30 +410,106 @@ static gbu_result run_host(gbu_ctx *c, Op op, const void *h_in, uint64_t n, void
     if (n >= kMaxUnits) return make(GBU_INVALID_ARG);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (!ok(cudaSetDevice(c->device))) return make(GBU_DEVICE_ERROR);
-    const size_t in_bytes = utf16_in(op) ? 2 * n : n;
-    const size_t ub = utf16_in(op) ? 1 : 2;
-    const size_t in_al = (in_bytes + 255) & ~size_t(255);
-    const size_t need = in_al + cap * ub + 16;
+    const bool u16 = utf16_in(op);
+    const uint64_t uin = u16 ? 2 : 1;                 // input unit bytes
+    const uint64_t ub = u16 ? 1 : 2;                  // output unit bytes
+    const uint64_t per_unit = u16 ? 3 : 1;            // worst-case output units per input unit
+    const uint64_t in_bytes = n * uin;
+    // slice cut points (input units), each at a character boundary
+    uint64_t cuts[kMaxSlices + 1];
+    int ns = (int)std::min<uint64_t>(kMaxSlices, std::max<uint64_t>(1, in_bytes / kMinSliceBytes));
+    const uint8_t *hb = static_cast<const uint8_t *>(h_in);
+    cuts[0] = 0;
+    for (int k = 1; k < ns; k++) {
+        uint64_t cu = std::max(cuts[k - 1], n * k / ns);
+        if (u16) {
+            const uint16_t *hw = static_cast<const uint16_t *>(h_in);
+            if (cu < n && (hw[cu] & 0xFC00u) == 0xDC00u) cu++;        // not between a pair
+        } else {
+            for (int t = 0; t < 3 && cu < n && (hb[cu] & 0xC0u) == 0x80u; t++) cu++;
+        }
+        cuts[k] = std::min(cu, n);
+    }
+    cuts[ns] = n;
+    // device staging: the input, then each slice's worst-case output
+    const uint64_t in_al = (in_bytes + 255) & ~uint64_t(255);
+    uint64_t out_base[kMaxSlices + 1];
+    out_base[0] = in_al;
+    for (int k = 0; k < ns; k++)
+        out_base[k + 1] = out_base[k] + (((cuts[k + 1] - cuts[k]) * per_unit * ub + 255) & ~uint64_t(255));
+    const uint64_t need = out_base[ns] + 16;
     if (need > c->io_bytes) {
-        if (!ok(cudaStreamSynchronize(s))) return make(GBU_DEVICE_ERROR);
+        if (!ok(cudaStreamSynchronize(s)) || !ok(cudaDeviceSynchronize())) return make(GBU_DEVICE_ERROR);
         if (c->io) cudaFree(c->io);
         c->io = nullptr;
         c->io_bytes = 0;
         if (!ok(cudaMalloc(&c->io, need))) return make(GBU_DEVICE_ERROR);
         c->io_bytes = need;
     }
-    uint8_t *d_in = c->io, *d_out = c->io + in_al;
-    if (!ok(cudaMemcpyAsync(d_in, h_in, in_bytes, cudaMemcpyHostToDevice, s)))
-        return make(GBU_DEVICE_ERROR);
-    gbu_result r = run_sync(c, op, d_in, n, d_out, cap, true, stream);
-    if (r.status >= GBU_INVALID_ARG) return r;
-    const uint64_t keep = r.out_len < cap ? r.out_len : cap;
-    if (keep) {
-        if (!ok(cudaMemcpyAsync(h_out, d_out, keep * ub, cudaMemcpyDeviceToHost, s)) ||
-            !ok(cudaStreamSynchronize(s)))
+    if (ns == 1) {   // one slice: copy in, transcode, copy out
+        uint8_t *d_in = c->io, *d_out = c->io + in_al;
+        if (!ok(cudaMemcpyAsync(d_in, h_in, in_bytes, cudaMemcpyHostToDevice, s)))
             return make(GBU_DEVICE_ERROR);
+        gbu_result r = run_sync(c, op, d_in, n, d_out, cap, true, stream);
+        if (r.status >= GBU_INVALID_ARG) return r;
+        const uint64_t keep = r.out_len < cap ? r.out_len : cap;
+        if (keep) {
+            if (!ok(cudaMemcpyAsync(h_out, d_out, keep * ub, cudaMemcpyDeviceToHost, s)) ||
+                !ok(cudaStreamSynchronize(s)))
+                return make(GBU_DEVICE_ERROR);
+        }
+        return r;
     }
-    return r;
+    if (!host_pipeline_ready(c)) return make(GBU_DEVICE_ERROR);
+    // scratch for the largest slice, before anything is enqueued
+    uint64_t max_units = 0;
+    for (int k = 0; k < ns; k++) max_units = std::max(max_units, cuts[k + 1] - cuts[k]);
+    if (ensure_scratch(c, (16 + max_units * uin + kChunkBytes - 1) / kChunkBytes + 1, s) != GBU_OK)
+        return make(GBU_DEVICE_ERROR);
+    if (!ok(cudaStreamSynchronize(s))) return make(GBU_DEVICE_ERROR);
+    // copy-in and kernels for every slice
+    for (int k = 0; k < ns; k++) {
+        const uint64_t u0 = cuts[k], nu = cuts[k + 1] - cuts[k];
+        if (!ok(cudaMemcpyAsync(c->io + u0 * uin, hb + u0 * uin, nu * uin, cudaMemcpyHostToDevice,
+                                c->h2d)) ||
+            !ok(cudaEventRecord(c->ev_in[k], c->h2d)) || !ok(cudaStreamWaitEvent(s, c->ev_in[k], 0)))
+            return make(GBU_DEVICE_ERROR);
+        const int32_t st = enqueue(c, op, c->io + u0 * uin, nu, c->io + out_base[k], nu * per_unit,
+                                   true, reinterpret_cast<ResultSlot *>(c->d_slice_res + k), s);
+        if (st != GBU_OK || !ok(cudaEventRecord(c->ev_done[k], s))) {
+            cudaStreamSynchronize(s);
+            return make(st != GBU_OK ? st : GBU_DEVICE_ERROR);
+        }
+    }
+    // join the results in order; copy each slice's output out as it finishes
+    uint64_t out_off = 0;
+    gbu_result total = make(GBU_OK, n, 0);
+    for (int k = 0; k < ns; k++) {
+        if (!ok(cudaEventSynchronize(c->ev_done[k]))) return make(GBU_DEVICE_ERROR);
+        gbu_result r;
+        std::memcpy(&r, const_cast<const gbu_result *>(c->h_slice_res + k), sizeof r);
+        if (r.status >= GBU_INVALID_ARG) {
+            cudaStreamSynchronize(s);
+            cudaStreamSynchronize(c->d2h);
+            if (r.status == GBU_DEVICE_TIMEOUT || r.status == GBU_DEVICE_ERROR) c->dirty = true;
+            return r;
+        }
+        const uint64_t keep = out_off < cap ? std::min<uint64_t>(r.out_len, cap - out_off) : 0;
+        if (keep && !ok(cudaMemcpyAsync(static_cast<uint8_t *>(h_out) + out_off * ub,
+                                        c->io + out_base[k], keep * ub, cudaMemcpyDeviceToHost,
+                                        c->d2h)))
+            return make(GBU_DEVICE_ERROR);
+        if (r.status != GBU_OK) {   // an encoding error ends the input
+            total = make(r.status, cuts[k] + r.in_offset, out_off + r.out_len);
+            break;
+        }
+        out_off += r.out_len;
+        total.out_len = out_off;
+    }
+    if (!ok(cudaStreamSynchronize(s)) || !ok(cudaStreamSynchronize(c->d2h)))
+        return make(GBU_DEVICE_ERROR);
+    if (total.status == GBU_OK && total.out_len > cap) total.status = GBU_OUTPUT_TOO_SMALL;
+    return total;
 }
 
 gbu_result gbu_utf8_to_utf16le_host(gbu_ctx *c, const uint8_t *h_in, uint64_t n, uint16_t *h_out,

@@ -182,3 +182,45 @@ def test_batched_200k_strings(env):
             assert np.array_equal(got, want), i
     finally:
         assert gbu.gbu_set_tune(ctx, 4, 0) == gbu.GBU_OK
+
+
+@pytest.mark.parametrize("enc", [textgen.UTF8, textgen.UTF16])
+def test_host_buffer_pipeline(env, enc):
+    """The host-buffer calls on 256 MiB inputs (cut into slices that are copied
+    in, transcoded and copied out in a pipeline): valid text, an error in a
+    middle slice, an error right after a slice cut, and a too-small output,
+    each against the oracle."""
+    torch, pool, ctx = env
+    size = 256 << 20
+    t = textgen.generate("emoji", size, enc, seed=71, executor=pool, keep_cps=False, keep_lens=False)
+    n = t.data.size if enc == textgen.UTF8 else t.data.size // 2
+    cap = n if enc == textgen.UTF8 else 3 * n
+    ub = 2 if enc == textgen.UTF8 else 1
+    h_in = torch.from_numpy(t.data).pin_memory()
+    h_out = torch.empty(cap * ub, dtype=torch.uint8).pin_memory()
+    call = gbu.gbu_utf8_to_utf16le_host if enc == textgen.UTF8 else gbu.gbu_utf16le_to_utf8_host
+    ref_fn = oracle.utf8_to_utf16le if enc == textgen.UTF8 else oracle.utf16le_to_utf8
+
+    def check(data, capacity):
+        h_in.copy_(torch.from_numpy(data))
+        h_out.fill_(0xA5)
+        r = call(ctx, h_in.data_ptr(), n, h_out.data_ptr(), capacity, 0)
+        ref, out = ref_fn(data, capacity)
+        assert (r.status, r.in_offset, r.out_len) == (ref.status, ref.in_offset, ref.out_len)
+        keep = min(ref.out_len, capacity) * ub
+        assert np.array_equal(h_out[:keep].numpy(), out.view(np.uint8)[:keep])
+        assert (h_out[capacity * ub:].numpy() == 0xA5).all()
+
+    check(t.data, cap)
+    bad = t.data.copy()
+    if enc == textgen.UTF8:
+        bad[size // 2 + 12345] = 0xFF
+        bad2 = t.data.copy()
+        bad2[(size // 8) + 1] = 0x80         # near a slice cut (32 MiB slices)
+    else:
+        bad.view("<u2")[n // 2 + 999] = 0xDC00
+        bad2 = t.data.copy()
+        bad2.view("<u2")[(n // 8) + 1] = 0xD800
+    check(bad, cap)
+    check(bad2, cap)
+    check(t.data, cap // 3)                    # OUTPUT_TOO_SMALL with the required length

@@ -56,7 +56,7 @@ struct gbu_ctx {
     unsigned int *d_item_done = nullptr;
     uint64_t items_cap = 0, chunk_map_cap = 0;
     uint32_t batch_items = 0, batch_chunks = 0;
-    bool batch_write = false;
+    bool batch_write = false, batch_be = false;
     cudaStream_t capture_stream = nullptr;
     cudaGraphExec_t graph = nullptr;
     gbu::Tune tune;                   // launch parameters of every call on the context
@@ -167,7 +167,7 @@ int32_t enqueue(gbu_ctx *c, Op op, const void *in, uint64_t n, void *out, uint64
     int grid = job_grid(c->device, c->tune);
     if (grid <= 0) return GBU_DEVICE_ERROR;
     if ((uint32_t)grid > J.total_chunks) grid = (int)J.total_chunks;
-    const cudaError_t e = launch_job(J, write, grid, stream, c->tune.look);
+    const cudaError_t e = launch_job(J, write, grid, stream, c->tune.look, big_endian(op));
     g_launches.fetch_add(1, std::memory_order_relaxed);
     if (!ok(e)) {
         c->dirty = true;
@@ -566,7 +566,7 @@ int32_t gbu_batch_plan(gbu_ctx *c, const gbu_batch_item *items, uint32_t count,
     if (!ok(cudaSetDevice(c->device))) return GBU_DEVICE_ERROR;
     // validate and count chunks
     uint64_t chunks = 0;
-    bool any_write = false;
+    bool any_write = false, any_be = false;
     for (uint32_t i = 0; i < count; i++) {
         const gbu_batch_item &b = items[i];
         if (b.op < GBU_OP_UTF8_TO_UTF16LE || b.op > GBU_OP_UTF8_LENGTH_FROM_UTF16BE)
@@ -578,6 +578,7 @@ int32_t gbu_batch_plan(gbu_ctx *c, const gbu_batch_item *items, uint32_t count,
         if (write && b.cap && !b.out) return GBU_INVALID_ARG;
         if (write && !utf16 && (reinterpret_cast<uintptr_t>(b.out) & 1u)) return GBU_INVALID_ARG;
         any_write |= write;
+        any_be |= op_big_endian(b.op);
         const uint64_t units = utf16 ? kChunk16 : kChunk8;
         const uint64_t head = b.n ? (utf16 ? ((reinterpret_cast<uintptr_t>(b.in) & 15u) >> 1)
                                            : (reinterpret_cast<uintptr_t>(b.in) & 15u))
@@ -616,6 +617,7 @@ int32_t gbu_batch_plan(gbu_ctx *c, const gbu_batch_item *items, uint32_t count,
     c->batch_items = count;
     c->batch_chunks = (uint32_t)chunks;
     c->batch_write = any_write;
+    c->batch_be = any_be;
     if (c->graph) {
         cudaGraphExecDestroy(c->graph);
         c->graph = nullptr;
@@ -638,7 +640,7 @@ static int32_t batch_enqueue(gbu_ctx *c, cudaStream_t s, bool counted = true)
     int grid = job_grid(c->device, c->tune);
     if (grid <= 0) return GBU_DEVICE_ERROR;
     if ((uint32_t)grid > J.total_chunks) grid = (int)J.total_chunks;
-    const cudaError_t e = launch_job(J, c->batch_write, grid, s, c->tune.look);
+    const cudaError_t e = launch_job(J, c->batch_write, grid, s, c->tune.look, c->batch_be);
     if (counted) g_launches.fetch_add(1, std::memory_order_relaxed);
     return ok(e) ? GBU_OK : GBU_DEVICE_ERROR;
 }

@@ -43,7 +43,9 @@ int job_max_ctas_per_sm(int device);
 int job_grid(int device, const Tune &t);
 int job_max_grid(int device);
 
-cudaError_t launch_job(const Job &J, bool write, int grid, cudaStream_t stream, int look = 8);
+// `be`: the job holds UTF-16BE items (selects a kernel with the byte swaps).
+cudaError_t launch_job(const Job &J, bool write, int grid, cudaStream_t stream,
+                       int look = GBU_DEFAULT_LOOK, bool be = false);
 cudaError_t launch_write_result(ResultSlot *dst, int32_t status, uint64_t in_offset,
                                 uint64_t out_len, cudaStream_t stream);
 

@@ -275,10 +275,10 @@ __device__ __forceinline__ uint32_t chunk8_phase1(St8 &st, const uint8_t *stage,
 }
 
 // Exact first error (flagged threads) and staging of the units.
-template <bool kWrite>
+template <bool kWrite, bool kBE>
 __device__ __forceinline__ void chunk8_phase2(St8 &st, const uint8_t *stage, uint8_t *obuf,
                                               uint32_t t_off, int64_t vt, int64_t lo, int64_t hi,
-                                              unsigned long long *s_err, bool be)
+                                              unsigned long long *s_err)
 {
     if (st.skip) return;
     // Threads straddling an end of the input see the bytes outside it as
@@ -325,7 +325,7 @@ __device__ __forceinline__ void chunk8_phase2(St8 &st, const uint8_t *stage, uin
             wa = ((ha & hma) | (wa & ~hma)) | (lma & 0xDC00DC00u);
             wb = ((hb & hmb) | (wb & ~hmb)) | (lmb & 0xDC00DC00u);
         }
-        if (be) {   // UTF-16BE output
+        if (kBE) {   // UTF-16BE output
             wa = prmt(wa, 0, 0x2301);
             wb = prmt(wb, 0, 0x2301);
         }
@@ -400,8 +400,9 @@ __device__ __forceinline__ uint32_t unit_keep(int64_t u, int64_t lo, int64_t hi)
     return (u >= lo && u < hi) ? 0xFFFFu : 0u;
 }
 
+template <bool kBE>
 __device__ __forceinline__ uint32_t chunk16_phase1(St16 &st, const uint8_t *stage, int64_t vt,
-                                                   int64_t lo, int64_t hi, bool be)
+                                                   int64_t lo, int64_t hi)
 {
     const uint8_t *sp = stage + kHalo + 32 * threadIdx.x;
     const uint4 a = *reinterpret_cast<const uint4 *>(sp);
@@ -442,7 +443,7 @@ __device__ __forceinline__ uint32_t chunk16_phase1(St16 &st, const uint8_t *stag
         w[0] &= unit_keep(vt - 2, lo, hi) | (unit_keep(vt - 1, lo, hi) << 16);
         w[9] &= unit_keep(vt + 16, lo, hi) | (unit_keep(vt + 17, lo, hi) << 16);
     }
-    if (be) {   // UTF-16BE: swap the bytes of every word once, then as UTF-16LE
+    if (kBE) {   // UTF-16BE: swap the bytes of every word once, then as UTF-16LE
 #pragma unroll
         for (int j = 0; j < 10; j++) w[j] = prmt(w[j], 0, 0x2301);
     }
@@ -694,7 +695,7 @@ constexpr int kDepth = GBU_OUT_DEPTH;
 constexpr int kSlots = 8;
 static_assert(kSlots > kDepth + 1, "hand-over slots");
 
-template <bool kWrite, int kLook>
+template <bool kWrite, int kLook, bool kAnyBE>
 __global__ void __launch_bounds__(kBlock, kMinBlocks)
 transcode_kernel(const Job J)
 {
@@ -902,7 +903,9 @@ transcode_kernel(const Job J)
         if (I.op & kOpUtf16) {
             const int64_t vt = (int64_t)k * kChunk16 + 16 * tid;
             St16 st;
-            const uint32_t cnt = chunk16_phase1(st, stage, vt, lo, hi, (I.op & kOpBE) != 0);
+            const uint32_t cnt = (kAnyBE && (I.op & kOpBE))
+                                     ? chunk16_phase1<true>(st, stage, vt, lo, hi)
+                                     : chunk16_phase1<false>(st, stage, vt, lo, hi);
             t_off = block_exclusive_scan(cnt, s_warp, &agg);
             hand_over();
             if (iter >= kDepth && cw_sync_or(!write_out(iter - kDepth))) {
@@ -920,7 +923,10 @@ transcode_kernel(const Job J)
                 failed = true;
                 break;
             }
-            chunk8_phase2<kWrite>(st, stage, obuf, t_off, vt, lo, hi, &s_err[p], (I.op & kOpBE) != 0);
+            if (kAnyBE && (I.op & kOpBE))
+                chunk8_phase2<kWrite, true>(st, stage, obuf, t_off, vt, lo, hi, &s_err[p]);
+            else
+                chunk8_phase2<kWrite, false>(st, stage, obuf, t_off, vt, lo, hi, &s_err[p]);
         }
         // every thread read this iteration's R.item[slot] at its start: the
         // slot's descriptor can be replaced by the one the next load needs
@@ -948,20 +954,22 @@ size_t job_smem_bytes(bool write)
     return (size_t)kStages * kStageBytes + (write ? (size_t)kDepth * kOutBufBytes : 0);
 }
 
-// Every instantiation of the kernel: (write, look-back width).
+// Every instantiation of the kernel: (write, look-back width, whether any
+// item is UTF-16BE; the UTF-16LE-only kernels carry no byte-order code).
 template <bool W, int L>
-constexpr const void *kernel_fn()
+const void *kernel_fn(bool be)
 {
-    return reinterpret_cast<const void *>(&transcode_kernel<W, L>);
+    return be ? reinterpret_cast<const void *>(&transcode_kernel<W, L, true>)
+              : reinterpret_cast<const void *>(&transcode_kernel<W, L, false>);
 }
 
-const void *kernel_for(bool write, int look)
+const void *kernel_for(bool write, int look, bool be)
 {
     switch (look) {
-    case 2: return write ? kernel_fn<true, 2>() : kernel_fn<false, 2>();
-    case 8: return write ? kernel_fn<true, 8>() : kernel_fn<false, 8>();
-    case 16: return write ? kernel_fn<true, 16>() : kernel_fn<false, 16>();
-    default: return write ? kernel_fn<true, 4>() : kernel_fn<false, 4>();
+    case 2: return write ? kernel_fn<true, 2>(be) : kernel_fn<false, 2>(be);
+    case 8: return write ? kernel_fn<true, 8>(be) : kernel_fn<false, 8>(be);
+    case 16: return write ? kernel_fn<true, 16>(be) : kernel_fn<false, 16>(be);
+    default: return write ? kernel_fn<true, 4>(be) : kernel_fn<false, 4>(be);
     }
 }
 
@@ -974,10 +982,12 @@ int job_max_ctas_per_sm(int device)
         return 0;
     for (const int look : kLookWidths)
         for (int w = 0; w < 2; w++)
-            if (cudaFuncSetAttribute(kernel_for(w != 0, look), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)job_smem_bytes(w != 0)) != cudaSuccess)
-                return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel_for(true, GBU_DEFAULT_LOOK), kBlock,
+            for (int be = 0; be < 2; be++)
+                if (cudaFuncSetAttribute(kernel_for(w != 0, look, be != 0),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)job_smem_bytes(w != 0)) != cudaSuccess)
+                    return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel_for(true, GBU_DEFAULT_LOOK, false), kBlock,
                                                       job_smem_bytes(true)) != cudaSuccess ||
         per < 1)
         per = 1;
@@ -999,10 +1009,10 @@ int job_max_grid(int device)
     return job_grid(device, Tune{});
 }
 
-cudaError_t launch_job(const Job &J, bool write, int grid, cudaStream_t stream, int look)
+cudaError_t launch_job(const Job &J, bool write, int grid, cudaStream_t stream, int look, bool be)
 {
     void *args[] = {const_cast<Job *>(&J)};
-    return cudaLaunchKernel(kernel_for(write, look), dim3(grid), dim3(kBlock), args,
+    return cudaLaunchKernel(kernel_for(write, look, be), dim3(grid), dim3(kBlock), args,
                             job_smem_bytes(write), stream);
 }
 

@@ -219,7 +219,7 @@ int32_t gbu_batch_launch_graph(gbu_ctx *ctx, void *stream);
 
 /* Launch parameters of a context (a tuning, not part of the paper's method:
  * results never depend on them). look_width: status words each lane of the
- * look-back warp reads per round (2, 4, 8 or 16; the 32 * look_width nearest
+ * look-back warp reads per round (1, 2, 4, 8 or 16; the 32 * look_width nearest
  * predecessors per round). ctas_per_sm: resident CTAs per SM of the
  * persistent grid (0: as many as fit, 1..that maximum otherwise). */
 typedef struct gbu_tune {
@@ -227,7 +227,7 @@ typedef struct gbu_tune {
     int32_t ctas_per_sm;
 } gbu_tune;
 
-/* Read / set the context's launch parameters (default {4, 0}). Setting them
+/* Read / set the context's launch parameters (default {1, 0}). Setting them
  * drops the context's captured batch graph. GBU_INVALID_ARG for values
  * outside the ranges above. */
 int32_t gbu_get_tune(gbu_ctx *ctx, gbu_tune *tune);

@@ -84,6 +84,21 @@ constexpr uint64_t kValueMask = (1ull << 40) - 1;
 // sleeps ~0.1-1 us), sets the timeout flag and lets the CTA finish.
 constexpr uint32_t kSpinLimit = 1u << 21;
 
+// Back-off while polling (ns): look-back rounds that found a predecessor
+// not ready, and mbarrier waits after GBU_MBAR_SPINS plain polls.
+#ifndef GBU_LB_SLEEP_SHORT
+#define GBU_LB_SLEEP_SHORT 200
+#endif
+#ifndef GBU_LB_SLEEP_LONG
+#define GBU_LB_SLEEP_LONG 1000
+#endif
+#ifndef GBU_MBAR_SPINS
+#define GBU_MBAR_SPINS 4
+#endif
+#ifndef GBU_MBAR_SLEEP
+#define GBU_MBAR_SLEEP 500
+#endif
+
 struct ResultSlot {      // layout of gbu_result
     int32_t status;
     uint32_t reserved;
@@ -253,7 +268,7 @@ __device__ __forceinline__ uint64_t lookback(const unsigned long long *status, u
             if (lane == 0) atomicOr(flags, 1u);
             return excl;
         }
-        __nanosleep(rounds < 8 ? 32 : 256);
+        __nanosleep(rounds < 8 ? GBU_LB_SLEEP_SHORT : GBU_LB_SLEEP_LONG);
     }
 }
 
@@ -395,7 +410,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
 {
     for (uint32_t i = 0; i < kSpinLimit; i++) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (i > 16) __nanosleep(64);
+        if (i > GBU_MBAR_SPINS) __nanosleep(GBU_MBAR_SLEEP);
     }
     return false;
 }

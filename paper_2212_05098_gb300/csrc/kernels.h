@@ -27,9 +27,9 @@ Item make_item(const void *in, uint64_t n, bool utf16, void *out, uint64_t cap, 
 
 // Tuning parameters of a launch: look-back width (status words per lane per
 // round, one of kLookWidths) and resident CTAs per SM (0: as many as fit).
-constexpr int kLookWidths[] = {2, 4, 8, 16};
+constexpr int kLookWidths[] = {1, 2, 4, 8, 16};
 #ifndef GBU_DEFAULT_LOOK
-#define GBU_DEFAULT_LOOK 4
+#define GBU_DEFAULT_LOOK 1
 #endif
 struct Tune {
     int look = GBU_DEFAULT_LOOK;

@@ -966,6 +966,7 @@ const void *kernel_fn(bool be)
 const void *kernel_for(bool write, int look, bool be)
 {
     switch (look) {
+    case 1: return write ? kernel_fn<true, 1>(be) : kernel_fn<false, 1>(be);
     case 2: return write ? kernel_fn<true, 2>(be) : kernel_fn<false, 2>(be);
     case 8: return write ? kernel_fn<true, 8>(be) : kernel_fn<false, 8>(be);
     case 16: return write ? kernel_fn<true, 16>(be) : kernel_fn<false, 16>(be);

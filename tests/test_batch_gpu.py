@@ -219,7 +219,7 @@ def test_batch_invalid_items(ctx):
     assert gbu.gbu_batch_plan(ctx, [(p, 4, p, 4, 0)], 0, 0) == gbu.GBU_INVALID_ARG
 
 
-@pytest.mark.parametrize("look", [2, 4, 8, 16])
+@pytest.mark.parametrize("look", [1, 2, 4, 8, 16])
 def test_results_do_not_depend_on_tuning(ctx, look):
     """Every (look-back width, CTAs per SM) gives the oracle's results, for a
     batch and for single-buffer calls."""
@@ -243,7 +243,7 @@ def test_results_do_not_depend_on_tuning(ctx, look):
             check_u8(ctx, bad8)
             check_u16(ctx, t16.data)
     finally:
-        assert gbu.gbu_set_tune(ctx, 4, 0) == gbu.GBU_OK
+        assert gbu.gbu_set_tune(ctx, 1, 0) == gbu.GBU_OK
     torch.cuda.synchronize()
 
 
@@ -252,7 +252,7 @@ def test_tune_rejects_bad_values(ctx):
     assert gbu.gbu_set_tune(ctx, 8, -1) == gbu.GBU_INVALID_ARG
     assert gbu.gbu_set_tune(ctx, 8, 1000) == gbu.GBU_INVALID_ARG
     t = gbu.gbu_get_tune(ctx)
-    assert (t.look_width, t.ctas_per_sm) == (4, 0)
+    assert (t.look_width, t.ctas_per_sm) == (1, 0)
 
 
 def test_autotune_and_cache(ctx, tmp_path):
@@ -263,17 +263,17 @@ def test_autotune_and_cache(ctx, tmp_path):
     cache = str(tmp_path / "tune.txt")
     try:
         st, t = gbu.gbu_batch_autotune(ctx, 0, cache)
-        assert st == gbu.GBU_OK and t.look_width in (2, 4, 8, 16) and 1 <= t.ctas_per_sm <= 3
+        assert st == gbu.GBU_OK and t.look_width in (1, 2, 4, 8, 16) and 1 <= t.ctas_per_sm <= 3
         lines = [l for l in open(cache) if l.strip()]
         assert len(lines) == 1 and lines[0].split()[1:3] == [str(t.look_width), str(t.ctas_per_sm)]
         # a cached key is taken without timing and without a new line
-        assert gbu.gbu_set_tune(ctx, 4, 0) == gbu.GBU_OK
+        assert gbu.gbu_set_tune(ctx, 1, 0) == gbu.GBU_OK
         st2, t2 = gbu.gbu_batch_autotune(ctx, 0, cache)
         assert st2 == gbu.GBU_OK and (t2.look_width, t2.ctas_per_sm) == (t.look_width, t.ctas_per_sm)
         assert len([l for l in open(cache) if l.strip()]) == 1
         _run(ctx, b, gbu.gbu_batch_launch_graph)
     finally:
-        assert gbu.gbu_set_tune(ctx, 4, 0) == gbu.GBU_OK
+        assert gbu.gbu_set_tune(ctx, 1, 0) == gbu.GBU_OK
 
 
 def test_batch_big_endian_ops(ctx):

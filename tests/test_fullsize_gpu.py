@@ -181,7 +181,7 @@ def test_batched_200k_strings(env):
             got = d_out[int(off[i]):int(off[i]) + want.size].cpu().numpy()
             assert np.array_equal(got, want), i
     finally:
-        assert gbu.gbu_set_tune(ctx, 4, 0) == gbu.GBU_OK
+        assert gbu.gbu_set_tune(ctx, 1, 0) == gbu.GBU_OK
 
 
 @pytest.mark.parametrize("enc", [textgen.UTF8, textgen.UTF16])

@@ -163,3 +163,39 @@ def test_submit_rejects(env):
         assert gbu.gbu_server_create(0, 1 << 20, 0, 16) is None
     finally:
         gbu.gbu_server_destroy(srv)
+
+
+def test_big_endian_requests(env):
+    """UTF-16BE requests through the server equal the single-buffer calls."""
+    torch, corpora, d_corp, ctx = env
+    srv = gbu.gbu_server_create(0, 64 << 20, 2, 64)
+    assert srv
+    try:
+        reqs, keep = [], []
+        for i, (prof, enc, data) in enumerate(corpora):
+            src = data[: 200_000 + 1000 * i]
+            if enc == textgen.UTF16:
+                src = src.reshape(-1, 2)[:, ::-1].reshape(-1).copy()       # as UTF-16BE
+                op, n = gbu.GBU_OP_UTF16BE_TO_UTF8, src.size // 2
+                cap_b = 3 * n
+            else:
+                op, n = gbu.GBU_OP_UTF8_TO_UTF16BE, src.size
+                cap_b = 2 * n
+            d_in = torch.from_numpy(src).cuda()
+            d_out = torch.full((cap_b + 64,), 0xA5, dtype=torch.uint8, device="cuda")
+            keep.append((d_in, d_out, op, n, cap_b, src))
+            reqs.append((op, d_in.data_ptr(), n, d_out.data_ptr(), cap_b, i))
+        st, comp = gbu.gbu_server_replay(srv, reqs, [0.0] * len(reqs), 60.0)
+        assert st == gbu.GBU_OK
+    finally:
+        gbu.gbu_server_destroy(srv)
+    torch.cuda.synchronize()
+    for i, (d_in, d_out, op, n, cap_b, src) in enumerate(keep):
+        c = comp[i]
+        if op == gbu.GBU_OP_UTF16BE_TO_UTF8:
+            ref, out = oracle.utf16be_to_utf8(src)
+        else:
+            ref, out = oracle.utf8_to_utf16be(src)
+        assert (c.result.status, c.result.in_offset, c.result.out_len) == \
+            (ref.status, ref.in_offset, ref.out_len), i
+        assert np.array_equal(d_out[: out.size].cpu().numpy(), out), i

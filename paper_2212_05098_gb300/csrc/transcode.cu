@@ -251,23 +251,26 @@ __device__ __forceinline__ uint32_t chunk8_phase1(St8 &st, const uint8_t *stage,
     st.warp3 = __any_sync(kFull, any3 != 0);
     st.warp4 = __any_sync(kFull, any4 != 0);
     if (st.warp3) {
-        // E0 + 80..9F (overlong), ED + A0..BF (surrogate); may over-flag
+        // E0 + 80..9F (overlong), ED + A0..BF (surrogate): a byte that is E0
+        // when bit 5 of the next byte is clear, or ED when it is set
 #pragma unroll
         for (int j = 1; j <= 8; j++) {
-            const uint32_t y5 = ahead(w[j], w[j + 1], 8) << 2;   // bit 5 of the next byte
-            bad |= zero_bytes(w[j] ^ 0xE0E0E0E0u) & ~y5;
-            bad |= zero_bytes(w[j] ^ 0xEDEDEDEDu) & y5;
+            const uint32_t y5 = ahead(w[j], w[j + 1], 8) << 2;   // bit 5 of the next byte, at bit 7
+            const uint32_t m = ((y5 >> 7) & 0x01010101u) * 0x0Du;  // 0x0D where it is set
+            bad |= zero_bytes(w[j] ^ 0xE0E0E0E0u ^ m);
         }
     }
     if (st.warp4) {
-        // F0 + 80..8F (overlong), F4 + 90..BF (too large), F5..FF; may over-flag
+        // F0 + 80..8F (overlong), F4 + 90..BF (too large): a byte that is F0
+        // when bits 5 and 4 of the next byte are clear, or F4 when one is
+        // set; and F5..FF (the low 7 bits reach 0x80 when 0x0B is added)
 #pragma unroll
         for (int j = 1; j <= 8; j++) {
             const uint32_t y = ahead(w[j], w[j + 1], 8);
-            const uint32_t y54 = (y << 2) | (y << 3);              // bits 5 or 4 of the next byte
-            bad |= zero_bytes(w[j] ^ 0xF0F0F0F0u) & ~y54;
-            bad |= zero_bytes(w[j] ^ 0xF4F4F4F4u) & y54;
-            bad |= classify(w[j]).c4 & (((w[j] & 0x0F0F0F0Fu) + 0x0B0B0B0Bu) << 3);
+            const uint32_t y54 = (y << 2) | (y << 3);              // bit 7: bit 5 or 4 of the next byte
+            const uint32_t m = (y54 >> 5) & 0x04040404u;           // 0x04 where set
+            bad |= zero_bytes(w[j] ^ 0xF0F0F0F0u ^ m);
+            bad |= ((w[j] & 0x7F7F7F7Fu) + 0x0B0B0B0Bu) & w[j] & 0x80808080u;
         }
     }
     st.bad = bad;

@@ -471,6 +471,35 @@ __device__ __forceinline__ uint32_t chunk16_phase1(St16 &st, const uint8_t *stag
     return cnt;
 }
 
+// UTF-8 bytes of 16 BMP units (no surrogates), two units at a time on
+// 16-bit lanes (Fig. 1(a)): lead F (the unit itself, C0 | u >> 6, or
+// E0 | u >> 12), second byte S (80 | u & 3F, or 80 | (u >> 6) & 3F in the
+// 3-byte form) and third byte T (80 | u & 3F); each unit stores its 1-3
+// bytes at p.
+__device__ __forceinline__ void encode_bmp(const uint32_t *w, uint8_t *p)
+{
+#pragma unroll
+    for (int j = 1; j <= 8; j++) {
+        const uint32_t x = w[j];
+        const uint32_t m2 = prmt(ge80_lanes(x), 0, 0xBB99);     // 0xFFFF on lanes >= 0x80
+        const uint32_t m3 = prmt(ge800_lanes(x), 0, 0xBB99);    // 0xFFFF on lanes >= 0x800
+        const uint32_t t = (x & 0x003F003Fu) | 0x00800080u;
+        const uint32_t x6 = x >> 6;
+        uint32_t f = (((x6 & 0x001F001Fu) | 0x00C000C0u) & m2) | (x & ~m2);
+        f = ((((x >> 12) & 0x000F000Fu) | 0x00E000E0u) & m3) | (f & ~m3);
+        const uint32_t s = (((x6 & 0x003F003Fu) | 0x00800080u) & m3) | (t & ~m3);
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const uint32_t u = (x >> (16 * h)) & 0xFFFFu;
+            const bool c2 = u >= 0x80u, c3 = u >= 0x800u;
+            p[0] = (uint8_t)(f >> (16 * h));
+            if (c2) p[1] = (uint8_t)(s >> (16 * h));
+            if (c3) p[2] = (uint8_t)(t >> (16 * h));
+            p += 1 + (c2 ? 1 : 0) + (c3 ? 1 : 0);
+        }
+    }
+}
+
 template <bool kWrite>
 __device__ __forceinline__ void chunk16_phase2(const St16 &st, uint8_t *obuf, uint32_t t_off,
                                                int64_t vt, int64_t lo, unsigned long long *s_err)
@@ -501,25 +530,41 @@ __device__ __forceinline__ void chunk16_phase2(const St16 &st, uint8_t *obuf, ui
         if (!kWrite) return;
         uint8_t *p = obuf + t_off;
         if (st.sur) {
-            // surrogate pairs: the high one emits the pair's 4 bytes, the
-            // low one nothing
+            // One encoder for every length (Fig. 1(a)): the code point (the
+            // pair's for a high surrogate, Sec. 7.3) split into 6-bit groups,
+            // most significant first, one per byte; the last `len` groups
+            // with their tags (F0/E0/C0 lead, 80 continuation).
+            // Each unit stores all 4 bytes at its offset and then advances by
+            // its true length: the bytes past its length are overwritten by
+            // the units after it, whose own output is at least that long (a
+            // low surrogate only follows a high one, which writes 4). The
+            // last 4 units store only their true length, so nothing is
+            // written past the thread's own output.
 #pragma unroll
             for (int i = 0; i < 16; i++) {
                 const uint32_t u = lane16(w, i), nx = lane16(w, i + 1);
                 const uint32_t t = u & 0xFC00u;
                 const bool is_hi = t == 0xD800u, is_lo = t == 0xDC00u;
                 const bool c2 = u >= 0x80u, c3 = u >= 0x800u;
-                uint32_t v = c3 ? enc3(u) : (c2 ? enc2(u) : u);
-                if (is_hi) {
-                    const uint32_t cp = (u << 10) + nx + 0xFCA02400u;
-                    v = (cp >> 18) | ((cp >> 4) & 0x3F00u) | ((cp << 10) & 0x3F0000u) |
-                        ((cp << 24) & 0x3F000000u) | 0x808080F0u;
-                }
+                const uint32_t c = is_hi ? (u << 10) + nx + 0xFCA02400u : u;
+                const uint32_t g = (c >> 18) | ((c >> 4) & 0x3F00u) | ((c << 10) & 0x3F0000u) |
+                                   ((c << 24) & 0x3F000000u);
                 const uint32_t len = is_lo ? 0u : (is_hi ? 4u : 1u + (c2 ? 1u : 0u) + (c3 ? 1u : 0u));
-                if (len >= 1) p[0] = (uint8_t)v;
-                if (len >= 2) p[1] = (uint8_t)(v >> 8);
-                if (len >= 3) p[2] = (uint8_t)(v >> 16);
-                if (len >= 4) p[3] = (uint8_t)(v >> 24);
+                const uint32_t tag = is_hi ? 0x808080F0u : (c3 ? 0x008080E0u : 0x000080C0u);
+                // (a shift by 32 - 8 * len; len = 0 gives g itself, unused)
+                uint32_t v = __funnelshift_r(g, 0u, 32u - 8u * len) | tag;
+                v = c2 ? v : u;
+                if (i < 12) {
+                    p[0] = (uint8_t)v;
+                    p[1] = (uint8_t)(v >> 8);
+                    p[2] = (uint8_t)(v >> 16);
+                    p[3] = (uint8_t)(v >> 24);
+                } else {
+                    if (len >= 1) p[0] = (uint8_t)v;
+                    if (len >= 2) p[1] = (uint8_t)(v >> 8);
+                    if (len >= 3) p[2] = (uint8_t)(v >> 16);
+                    if (len >= 4) p[3] = (uint8_t)(v >> 24);
+                }
                 p += len;
             }
         } else if (st.only12) {
@@ -533,16 +578,7 @@ __device__ __forceinline__ void chunk16_phase2(const St16 &st, uint8_t *obuf, ui
                 p += big ? 2 : 1;
             }
         } else {
-#pragma unroll
-            for (int i = 0; i < 16; i++) {
-                const uint32_t u = lane16(w, i);
-                const bool c2 = u >= 0x80u, c3 = u >= 0x800u;
-                const uint32_t v = c3 ? enc3(u) : (c2 ? enc2(u) : u);
-                p[0] = (uint8_t)v;
-                if (c2) p[1] = (uint8_t)(v >> 8);
-                if (c3) p[2] = (uint8_t)(v >> 16);
-                p += 1 + (c2 ? 1 : 0) + (c3 ? 1 : 0);
-            }
+            encode_bmp(w, p);
         }
         return;
     }

@@ -296,9 +296,10 @@ __device__ __forceinline__ void chunk8_phase2(St8 &st, const uint8_t *stage, uin
     uint32_t s[9], c3[9], c4[9];
 #pragma unroll
     for (int j = 0; j < 9; j++) {
-        const Cls c = classify(w[j]);
-        c3[j] = c.c3;
-        c4[j] = c.c4;
+        // >= E0 / >= F0 at bit 7 of each byte (the other bits are not
+        // used: the masks below replicate bit 7)
+        c3[j] = w[j] & (w[j] << 1) & (w[j] << 2);
+        c4[j] = c3[j] & (w[j] << 3);
         const uint32_t na = prmt(w[j], 0, 0xBA98);        // 0xFF where byte >= 0x80
         s[j] = w[j] & ~(na & 0xC0C0C0C0u);                // tag bits stripped
     }

@@ -345,19 +345,24 @@ __device__ __forceinline__ void chunk8_phase2(St8 &st, const uint8_t *stage, uin
 // UTF-16LE -> UTF-8 chunk (paper Sec. 7)
 //
 // Output length per word (Sec. 7, plan of attack): 1 byte below U+0080, 2
-// below U+0800, 3 for other BMP words, 4 for a high surrogate (the pair), 0
-// for a low surrogate; counted two words at a time on 16-bit lanes.
+// below U+0800, 3 for other BMP words, and 2 for each half of a surrogate
+// pair: the pair's 4 bytes are split between its two words (the high one
+// holds the code point's bits 20-12, the low one, with the high word's
+// last 2 bits, bits 11-0), so that no word depends on the word after it and
+// a pair that crosses a thread or chunk boundary needs no special case.
+// Counted two words at a time on 16-bit lanes.
 //
 // Paths: like the paper's fast paths (Sec. 7.1), each warp picks one from its
 // own words: all below U+0800 (1-2 byte encoder), no surrogates (1-3 byte
 // encoder) - neither needs validation - or the general path with the
-// surrogate join and the sequencing check of Sec. 7.4: a high surrogate not
-// followed by a low one is LONE_HIGH at the high, a low surrogate not
-// preceded by a high one is LONE_LOW at the low.
+// sequencing check of Sec. 7.4: a high surrogate not followed by a low one
+// is LONE_HIGH at the high, a low surrogate not preceded by a high one is
+// LONE_LOW at the low.
 //
-// Encoding (Fig. 1(a), Sec. 7.2-7.3): pairs are joined with
-// (hi << 10) + lo + 0xFCA02400 (32-bit wrap); the 6-bit groups of the code
-// point get the tag bits C0/E0/F0 (lead) and 80 (continuation).
+// Encoding (Fig. 1(a), Sec. 7.2-7.3): the 6-bit groups of the code point get
+// the tag bits C0/E0/F0 (lead) and 80 (continuation); for a pair, the code
+// point is 0x10000 + ((hi & 3FF) << 10) + (lo & 3FF), so its bits 20-10 are
+// (hi & 3FF) + 0x40.
 // ===========================================================================
 
 __device__ __forceinline__ uint32_t ge80_lanes(uint32_t w)    // word >= 0x0080, bit 15 per lane
@@ -456,13 +461,11 @@ __device__ __forceinline__ uint32_t chunk16_phase1(St16 &st, const uint8_t *stag
     for (int j = 0; j < 8; j++) {
         const uint32_t x = w[1 + j];
         const uint32_t ga = ge80_lanes(x), gb = ge800_lanes(x), s = surr_lanes(x);
-        const uint32_t lo_bit = (x << 5) & 0x80008000u;   // bit 10: low surrogate
         uint32_t vm = 0x80008000u;
         if (masked)
             vm = (((st.vmask >> (2 * j)) & 1u) << 15) | (((st.vmask >> (2 * j + 1)) & 1u) << 31);
-        // 1 + [>=80] + [>=800] + [high] - 3 [low]
-        cnt += __popc(vm) + __popc(ga & vm) + __popc(gb & vm) + __popc(s & ~lo_bit & vm) -
-               3u * __popc(s & lo_bit & vm);
+        // 1 + [>=80] + [>=800] - [surrogate]: 1-3 bytes, 2 for either half of a pair
+        cnt += __popc(vm) + __popc(ga & vm) + __popc(gb & vm) - __popc(s & vm);
         any800 |= gb;
         anysur |= s;
     }
@@ -472,27 +475,45 @@ __device__ __forceinline__ uint32_t chunk16_phase1(St16 &st, const uint8_t *stag
     return cnt;
 }
 
-// UTF-8 bytes of 16 BMP units (no surrogates), two units at a time on
-// 16-bit lanes (Fig. 1(a)): lead F (the unit itself, C0 | u >> 6, or
-// E0 | u >> 12), second byte S (80 | u & 3F, or 80 | (u >> 6) & 3F in the
-// 3-byte form) and third byte T (80 | u & 3F); each unit stores its 1-3
-// bytes at p.
+// UTF-8 bytes of 16 units, two units at a time on 16-bit lanes
+// (Fig. 1(a)): lead F (the unit itself, C0 | u >> 6, or E0 | u >> 12),
+// second byte S (80 | u & 3F, or 80 | (u >> 6) & 3F in the 3-byte form) and
+// third byte T (80 | u & 3F); each unit stores its 1-3 bytes at p.
+// A surrogate pair's 4 bytes (Sec. 7.3) are split between its halves, 2
+// each: with U = (high & 3FF) + 40 (the code point >> 10), the high
+// surrogate stores F0 | U >> 8 and 80 | (U >> 2) & 3F, the low one
+// 80 | (high & 3) << 4 | (low >> 6) & F and 80 | low & 3F.
+// kSur: the units may hold surrogates (validly paired; the pair may cross
+// into the next thread, the low half then stores its 2 bytes there).
+template <bool kSur>
 __device__ __forceinline__ void encode_bmp(const uint32_t *w, uint8_t *p)
 {
 #pragma unroll
     for (int j = 1; j <= 8; j++) {
         const uint32_t x = w[j];
         const uint32_t m2 = prmt(ge80_lanes(x), 0, 0xBB99);     // 0xFFFF on lanes >= 0x80
-        const uint32_t m3 = prmt(ge800_lanes(x), 0, 0xBB99);    // 0xFFFF on lanes >= 0x800
+        uint32_t m3 = prmt(ge800_lanes(x), 0, 0xBB99);          // 0xFFFF on lanes >= 0x800
         const uint32_t t = (x & 0x003F003Fu) | 0x00800080u;
         const uint32_t x6 = x >> 6;
         uint32_t f = (((x6 & 0x001F001Fu) | 0x00C000C0u) & m2) | (x & ~m2);
         f = ((((x >> 12) & 0x000F000Fu) | 0x00E000E0u) & m3) | (f & ~m3);
-        const uint32_t s = (((x6 & 0x003F003Fu) | 0x00800080u) & m3) | (t & ~m3);
+        uint32_t s = (((x6 & 0x003F003Fu) | 0x00800080u) & m3) | (t & ~m3);
+        if (kSur) {
+            const uint32_t sr = surr_lanes(x);
+            const uint32_t ms = prmt(sr, 0, 0xBB99);             // surrogate lanes
+            const uint32_t ml = prmt(sr & (x << 5), 0, 0xBB99);  // low-surrogate lanes
+            const uint32_t hu = (x & 0x03FF03FFu) + 0x00400040u;  // U of a high surrogate
+            const uint32_t fh = ((hu >> 8) & 0x00070007u) | 0x00F000F0u;
+            const uint32_t sh = ((hu >> 2) & 0x003F003Fu) | 0x00800080u;
+            const uint32_t prev = __funnelshift_l(w[j - 1], x, 16);   // the unit before each lane
+            const uint32_t fl = ((prev & 0x00030003u) << 4) | (x6 & 0x000F000Fu) | 0x00800080u;
+            f = (((fl & ml) | (fh & ~ml)) & ms) | (f & ~ms);
+            s = (((t & ml) | (sh & ~ml)) & ms) | (s & ~ms);
+            m3 &= ~ms;                                            // surrogates store 2 bytes
+        }
 #pragma unroll
         for (int h = 0; h < 2; h++) {
-            const uint32_t u = (x >> (16 * h)) & 0xFFFFu;
-            const bool c2 = u >= 0x80u, c3 = u >= 0x800u;
+            const bool c2 = (m2 >> (16 * h)) & 1u, c3 = (m3 >> (16 * h)) & 1u;
             p[0] = (uint8_t)(f >> (16 * h));
             if (c2) p[1] = (uint8_t)(s >> (16 * h));
             if (c3) p[2] = (uint8_t)(t >> (16 * h));
@@ -531,43 +552,7 @@ __device__ __forceinline__ void chunk16_phase2(const St16 &st, uint8_t *obuf, ui
         if (!kWrite) return;
         uint8_t *p = obuf + t_off;
         if (st.sur) {
-            // One encoder for every length (Fig. 1(a)): the code point (the
-            // pair's for a high surrogate, Sec. 7.3) split into 6-bit groups,
-            // most significant first, one per byte; the last `len` groups
-            // with their tags (F0/E0/C0 lead, 80 continuation).
-            // Each unit stores all 4 bytes at its offset and then advances by
-            // its true length: the bytes past its length are overwritten by
-            // the units after it, whose own output is at least that long (a
-            // low surrogate only follows a high one, which writes 4). The
-            // last 4 units store only their true length, so nothing is
-            // written past the thread's own output.
-#pragma unroll
-            for (int i = 0; i < 16; i++) {
-                const uint32_t u = lane16(w, i), nx = lane16(w, i + 1);
-                const uint32_t t = u & 0xFC00u;
-                const bool is_hi = t == 0xD800u, is_lo = t == 0xDC00u;
-                const bool c2 = u >= 0x80u, c3 = u >= 0x800u;
-                const uint32_t c = is_hi ? (u << 10) + nx + 0xFCA02400u : u;
-                const uint32_t g = (c >> 18) | ((c >> 4) & 0x3F00u) | ((c << 10) & 0x3F0000u) |
-                                   ((c << 24) & 0x3F000000u);
-                const uint32_t len = is_lo ? 0u : (is_hi ? 4u : 1u + (c2 ? 1u : 0u) + (c3 ? 1u : 0u));
-                const uint32_t tag = is_hi ? 0x808080F0u : (c3 ? 0x008080E0u : 0x000080C0u);
-                // (a shift by 32 - 8 * len; len = 0 gives g itself, unused)
-                uint32_t v = __funnelshift_r(g, 0u, 32u - 8u * len) | tag;
-                v = c2 ? v : u;
-                if (i < 12) {
-                    p[0] = (uint8_t)v;
-                    p[1] = (uint8_t)(v >> 8);
-                    p[2] = (uint8_t)(v >> 16);
-                    p[3] = (uint8_t)(v >> 24);
-                } else {
-                    if (len >= 1) p[0] = (uint8_t)v;
-                    if (len >= 2) p[1] = (uint8_t)(v >> 8);
-                    if (len >= 3) p[2] = (uint8_t)(v >> 16);
-                    if (len >= 4) p[3] = (uint8_t)(v >> 24);
-                }
-                p += len;
-            }
+            encode_bmp<true>(w, p);
         } else if (st.only12) {
 #pragma unroll
             for (int i = 0; i < 16; i++) {
@@ -579,7 +564,7 @@ __device__ __forceinline__ void chunk16_phase2(const St16 &st, uint8_t *obuf, ui
                 p += big ? 2 : 1;
             }
         } else {
-            encode_bmp(w, p);
+            encode_bmp<false>(w, p);
         }
         return;
     }
@@ -594,22 +579,22 @@ __device__ __forceinline__ void chunk16_phase2(const St16 &st, uint8_t *obuf, ui
         if (is_hi && (nx & 0xFC00u) != 0xDC00u) kind = kLoneHigh;
         if (is_lo && (pv & 0xFC00u) != 0xD800u) kind = kLoneLow;
         const bool c2 = u >= 0x80u, c3 = u >= 0x800u;
-        const uint32_t len = is_lo ? 0u : (is_hi ? 4u : 1u + (c2 ? 1u : 0u) + (c3 ? 1u : 0u));
+        const uint32_t len = (is_hi || is_lo) ? 2u : 1u + (c2 ? 1u : 0u) + (c3 ? 1u : 0u);
         uint32_t v;
-        if (is_hi) {
-            const uint32_t cp = (u << 10) + nx + 0xFCA02400u;
-            v = (cp >> 18) | ((cp >> 4) & 0x3F00u) | ((cp << 10) & 0x3F0000u) |
-                ((cp << 24) & 0x3F000000u) | 0x808080F0u;
+        if (is_hi) {            // the first 2 bytes of the pair's 4
+            const uint32_t hu = (u & 0x3FFu) + 0x40u;
+            v = (0xF0u | (hu >> 8)) | ((0x80u | ((hu >> 2) & 0x3Fu)) << 8);
+        } else if (is_lo) {     // the last 2
+            v = (0x80u | ((pv & 3u) << 4) | ((u >> 6) & 0xFu)) | ((0x80u | (u & 0x3Fu)) << 8);
         } else {
             v = c3 ? enc3(u) : (c2 ? enc2(u) : u);
         }
         if ((st.vmask >> i) & 1u) {
             if (kWrite && o + len <= kStage16Bytes) {
                 uint8_t *q = obuf + o;
-                if (len >= 1) q[0] = (uint8_t)v;
+                q[0] = (uint8_t)v;
                 if (len >= 2) q[1] = (uint8_t)(v >> 8);
                 if (len >= 3) q[2] = (uint8_t)(v >> 16);
-                if (len >= 4) q[3] = (uint8_t)(v >> 24);
             }
             if (kind != 0 && key == ~0ull) key = err_key((uint64_t)(vt + i - lo), kind, o);
             o += len;

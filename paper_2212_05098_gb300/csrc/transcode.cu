@@ -530,21 +530,20 @@ __device__ __forceinline__ void chunk16_phase2(const St16 &st, uint8_t *obuf, ui
     const uint32_t *w = st.w;
     bool slow = st.slow;
     if (st.sur && !slow) {
-        // sequencing (Sec. 7.4): every high surrogate is followed by a low
-        // one and every low one preceded by a high one; a thread holding a
-        // lone one takes the exact path below
+        // sequencing (Sec. 7.4): a word is a low surrogate exactly when the
+        // word before it is a high one; a thread where this fails for one of
+        // its words, or for the word after its last, takes the exact path
+        // below
         auto hi_lanes = [](uint32_t x) { return surr_lanes(x) & ~(x << 5); };
         auto lo_lanes = [](uint32_t x) { return surr_lanes(x) & (x << 5); };
-        uint32_t v = 0, h_prev = hi_lanes(w[0]), h_cur = hi_lanes(w[1]), l_cur = lo_lanes(w[1]);
+        uint32_t v = 0, h_prev = hi_lanes(w[0]);
 #pragma unroll
         for (int j = 1; j <= 8; j++) {
-            const uint32_t l_next = lo_lanes(w[j + 1]);
-            v |= (h_cur & ~__funnelshift_r(l_cur, l_next, 16)) |
-                 (l_cur & ~__funnelshift_l(h_prev, h_cur, 16));
-            h_prev = h_cur;
-            h_cur = hi_lanes(w[j + 1]);
-            l_cur = l_next;
+            const uint32_t h = hi_lanes(w[j]);
+            v |= __funnelshift_l(h_prev, h, 16) ^ lo_lanes(w[j]);
+            h_prev = h;
         }
+        v |= (h_prev ^ (lo_lanes(w[9]) << 16)) & 0x80000000u;
         slow = v != 0;
     }
     if (!slow) {

@@ -13,7 +13,9 @@ than the 129 MB L2, so no flush is needed between steps.
   roofline  the dominant kernel's algorithmic bytes (input + output) per
             launch / its CUDA-event launch time, against the measured HBM
             copy peak
-  cpu_baseline  the oracle (scalar C, one thread) on a bounded prefix sample
+  cpu_baseline  the oracle (scalar C, one thread) on a bounded prefix sample;
+            "parallel": the same sample cut at character boundaries and
+            converted on all host cores at once
 
 `--impl reference` times the oracle itself on the host cores (bounded sample
 per step) and prints the same JSON line with "impl": "reference".
@@ -222,6 +224,48 @@ def cpu_baseline(cases, sample_bytes):
             oracle.utf16le_to_utf8(d)
         total += d.size
     dt = time.perf_counter() - t0
+    return total, dt
+
+
+def _char_cuts(data, parts: int, utf16: bool):
+    """Byte offsets cutting `data` into `parts` pieces at character boundaries
+    (UTF-8: never before a continuation byte; UTF-16LE: never between the
+    halves of a surrogate pair)."""
+    n = int(data.size)
+    unit = 2 if utf16 else 1
+    cuts = [0]
+    for k in range(1, parts):
+        c = max((n * k // parts) // unit * unit, cuts[-1])
+        if utf16:
+            while c + 1 < n and 0xDC <= int(data[c + 1]) <= 0xDF:
+                c += 2
+        else:
+            while c < n and (int(data[c]) & 0xC0) == 0x80:
+                c += 1
+        cuts.append(min(c, n))
+    cuts.append(n)
+    return cuts
+
+
+def cpu_baseline_parallel(cases, sample_bytes, threads):
+    """The same sample, every buffer cut at character boundaries into
+    `threads` parts that the oracle converts on `threads` host threads at
+    once (its C calls release the GIL). Returns (bytes, seconds)."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    jobs = []
+    total = 0
+    for c in cases:
+        d = c["data"][: sample_bytes - (sample_bytes % 2)]
+        u16 = c["dir"] != "utf8_to_utf16le"
+        cuts = _char_cuts(d, threads, u16)
+        f = oracle.utf16le_to_utf8 if u16 else oracle.utf8_to_utf16le
+        jobs += [(f, d[a:b]) for a, b in zip(cuts[:-1], cuts[1:]) if b > a]
+        total += d.size
+    with ThreadPoolExecutor(threads) as ex:
+        t0 = time.perf_counter()
+        list(ex.map(lambda j: j[0](j[1]), jobs))
+        dt = time.perf_counter() - t0
     return total, dt
 
 
@@ -458,6 +502,12 @@ def main():
                "sample": f"oracle (scalar C, 1 thread) on the first "
                          f"{args.cpu_sample >> 20} MiB of each of the {len(cases)} buffers "
                          f"({b / 1e9:.2f} GB total, {dt:.1f} s)"}
+        nthreads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+        if nthreads and nthreads > 1:
+            bp, dtp = cpu_baseline_parallel(cases, args.cpu_sample, nthreads)
+            cpu["parallel"] = {"value": bp / dtp / 1e9, "unit": "GB/s", "cores": nthreads,
+                               "sample": "the same sample, each buffer cut at character "
+                                         f"boundaries into {nthreads} parts converted at once"}
 
     if rank == 0:
         line = {

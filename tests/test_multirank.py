@@ -139,3 +139,22 @@ def test_job_rate_and_rank_inputs():
     assert ms == 20.0                                          # the slowest rank's time
     assert abs(gbs - (local_bytes * 3) / 0.020 / 1e9) < 1e-9   # all ranks' bytes
     assert objs[0] != objs[1]                                  # ranks draw different text
+
+
+def test_parallel_oracle_cuts():
+    """The N-core oracle timing's cuts: at character boundaries, and the
+    parts' conversions concatenate to the whole buffer's."""
+    import bench
+    for prof, enc in (("emoji", textgen.UTF8), ("emoji", textgen.UTF16), ("cjk", textgen.UTF8)):
+        data = textgen.generate(prof, 300_001, enc, seed=9).data
+        u16 = enc == textgen.UTF16
+        f = oracle.utf16le_to_utf8 if u16 else oracle.utf8_to_utf16le
+        for parts in (1, 3, 16):
+            cuts = bench._char_cuts(data, parts, u16)
+            assert cuts[0] == 0 and cuts[-1] == data.size and cuts == sorted(cuts)
+            outs = []
+            for a, b in zip(cuts[:-1], cuts[1:]):
+                r, o = f(data[a:b])
+                assert r.status == 0
+                outs.append(o)
+            assert np.array_equal(np.concatenate(outs), f(data)[1])

@@ -9,7 +9,9 @@ than the 129 MB L2, so no flush is needed between steps.
 
   value     whole-job input GB/s (1e9 bytes/s) over all ranks, device-timed
   e2e       the same metric through the host-buffer C-ABI calls (input copied
-            host->device and output device->host inside the timed region)
+            host->device and output device->host inside the timed region);
+            "link_bound": the e2e value the measured host<->device copy rates
+            would allow with both directions busy all the time
   roofline  the dominant kernel's algorithmic bytes (input + output) per
             launch / its CUDA-event launch time, against the measured HBM
             copy peak
@@ -210,6 +212,38 @@ def gen_inputs(profiles, size, rank, pool):
                                  keep_cps=False, keep_lens=False)
             cases.append({"profile": prof, "dir": d, "data": t.data})
     return cases
+
+
+def host_link_gbs(torch, nbytes):
+    """Copy-engine rates between pinned host memory and HBM (GB/s): each
+    direction alone, and both at once on two streams."""
+    h_a = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    h_b = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    d_a = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    d_b = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def run(up, down, reps=3):
+        def once():
+            if up:
+                with torch.cuda.stream(s1):
+                    d_a.copy_(h_a, non_blocking=True)
+            if down:
+                with torch.cuda.stream(s2):
+                    h_b.copy_(d_b, non_blocking=True)
+        once()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            once()
+        torch.cuda.synchronize()
+        return nbytes * reps / (time.perf_counter() - t0) / 1e9
+
+    out = {"h2d": run(True, False), "d2h": run(False, True)}
+    both = run(True, True)
+    out["h2d_concurrent"] = out["d2h_concurrent"] = both
+    out["bytes"] = nbytes
+    return out
 
 
 def cpu_baseline(cases, sample_bytes):
@@ -477,6 +511,13 @@ def main():
         e2e = {"value": world * h2d * args.e2e_steps / dt / 1e9, "unit": "GB/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "steps": args.e2e_steps, "api": "gbu_*_host (pinned host buffers)"}
+        link = host_link_gbs(torch, 1 << 30)
+        # the best e2e value the host link allows: both directions at once, at
+        # the concurrent copy rates, and no time for anything else
+        t_link = max(h2d / (link["h2d_concurrent"] * 1e9), d2h / (link["d2h_concurrent"] * 1e9))
+        e2e["link"] = link
+        e2e["link_bound"] = world * h2d / t_link / 1e9
+        e2e["frac_of_link_bound"] = e2e["value"] / e2e["link_bound"]
 
     # validation only (no output, no look-back), same buffers, 3 passes
     vres = torch.zeros(4, dtype=torch.int64, device="cuda")

@@ -185,36 +185,48 @@ __device__ __forceinline__ uint32_t chunk8_phase1(St8 &st, const uint8_t *stage,
     w[5] = b.x; w[6] = b.y; w[7] = b.z; w[8] = b.w;
     w[0] = *reinterpret_cast<const uint32_t *>(sp - 4);
     w[9] = *reinterpret_cast<const uint32_t *>(sp + 32);
-    // threads wholly outside the input (the tail of an item's last chunk)
-    // count nothing; a warp wholly outside skips the chunk body
-    const bool outside = vt + 32 <= lo || vt >= hi;
-    st.skip = __all_sync(kFull, outside);
     st.bad = 0;
-    if (st.skip) {
-        st.vmask = 0;
-        st.warp3 = st.warp4 = false;
-        return 0;
-    }
     st.vmask = 0xFFFFFFFFu;
     bool masked = false;
-    if (outside) {
+    // A chunk whose bytes and context all lie inside the input (the common
+    // case; the test is the same for every thread) needs none of the edge
+    // handling below.
+    const int64_t v0 = vt - 32 * (int64_t)threadIdx.x;
+    const bool interior = v0 - 4 >= lo && v0 + (int64_t)kChunk8 + 4 <= hi;
+    if (!interior) {
+        // threads wholly outside the input (the tail of an item's last chunk)
+        // count nothing; a warp wholly outside skips the chunk body
+        const bool outside = vt + 32 <= lo || vt >= hi;
+        st.skip = __all_sync(kFull, outside);
+        if (st.skip) {
+            st.vmask = 0;
+            st.warp3 = st.warp4 = false;
+            return 0;
+        }
+        if (outside) {
 #pragma unroll
-        for (int j = 0; j < 10; j++) w[j] = 0;
-        st.vmask = 0;
-        masked = true;
-    } else if (vt < lo || vt + 32 > hi) {   // straddles an end of the input
-        masked = true;
-        st.vmask = 0;
+            for (int j = 0; j < 10; j++) w[j] = 0;
+            st.vmask = 0;
+            masked = true;
+        } else if (vt < lo || vt + 32 > hi) {   // straddles an end of the input
+            masked = true;
+            st.vmask = 0;
 #pragma unroll
-        for (int i = 0; i < 32; i++)
-            if (vt + i >= lo && vt + i < hi) st.vmask |= 1u << i;
+            for (int i = 0; i < 32; i++)
+                if (vt + i >= lo && vt + i < hi) st.vmask |= 1u << i;
 #pragma unroll
-        for (int j = 0; j < 8; j++) w[1 + j] = mask_word_bytes(w[1 + j], vt + 4 * j, lo, hi);
+            for (int j = 0; j < 8; j++) w[1 + j] = mask_word_bytes(w[1 + j], vt + 4 * j, lo, hi);
+        }
+        if (!outside && (vt - 4 < lo || vt + 36 > hi)) {
+            w[0] = mask_word_bytes(w[0], vt - 4, lo, hi);
+            w[9] = mask_word_bytes(w[9], vt + 32, lo, hi);
+        }
+    } else {
+        st.skip = false;
     }
-    if (!outside && (vt - 4 < lo || vt + 36 > hi)) {
-        w[0] = mask_word_bytes(w[0], vt - 4, lo, hi);
-        w[9] = mask_word_bytes(w[9], vt + 32, lo, hi);
-    }
+    // some thread of the warp masks its end positions (warp-uniform, so the
+    // unmasked warps branch around that work instead of predicating it)
+    const bool wmasked = !interior && __any_sync(kFull, masked);
 
     uint32_t bad = 0, any3, any4, cnt = 0;
     {
@@ -240,12 +252,21 @@ __device__ __forceinline__ uint32_t chunk8_phase1(St8 &st, const uint8_t *stage,
         const uint32_t exp9 = (cl[8].c2 >> 24) | (cl[8].c3 >> 16) | (cl[8].c4 >> 8);
         bad |= exp9 & ~cl[9].ct;
         ec[8] = exp9 & cl[9].ct;
+        if (!wmasked) {
 #pragma unroll
-        for (int j = 1; j <= 8; j++) {
-            uint32_t e = (~ahead(ec[j - 1], ec[j], 8) | back(cl[j - 1].c4, cl[j].c4, 16)) & kB7;
-            if (masked) e &= spread4((st.vmask >> (4 * (j - 1))) & 0xFu);
-            st.end[j - 1] = e;
-            cnt += __popc(e);
+            for (int j = 1; j <= 8; j++) {
+                const uint32_t e = (~ahead(ec[j - 1], ec[j], 8) | back(cl[j - 1].c4, cl[j].c4, 16)) & kB7;
+                st.end[j - 1] = e;
+                cnt += __popc(e);
+            }
+        } else {
+#pragma unroll
+            for (int j = 1; j <= 8; j++) {
+                uint32_t e = (~ahead(ec[j - 1], ec[j], 8) | back(cl[j - 1].c4, cl[j].c4, 16)) & kB7;
+                e &= spread4((st.vmask >> (4 * (j - 1))) & 0xFu);
+                st.end[j - 1] = e;
+                cnt += __popc(e);
+            }
         }
     }
     st.warp3 = __any_sync(kFull, any3 != 0);
@@ -421,53 +442,73 @@ __device__ __forceinline__ uint32_t chunk16_phase1(St16 &st, const uint8_t *stag
     w[5] = b.x; w[6] = b.y; w[7] = b.z; w[8] = b.w;
     w[0] = *reinterpret_cast<const uint32_t *>(sp - 4);
     w[9] = *reinterpret_cast<const uint32_t *>(sp + 32);
-    // threads wholly outside the input count nothing; a warp wholly outside
-    // skips the chunk body
-    const bool outside = vt + 16 <= lo || vt >= hi;
-    st.skip = __all_sync(kFull, outside);
-    bool edge = false;
-    if (st.skip) {
-        st.vmask = 0;
-        st.slow = st.sur = st.only12 = false;
-        return 0;
-    }
     st.vmask = 0xFFFFu;
-    bool masked = false;
-    if (outside) {
+    bool edge = false, masked = false;
+    // A chunk whose words and context all lie inside the input (the common
+    // case; the same test for every thread) needs none of the edge handling.
+    const int64_t v0 = vt - 16 * (int64_t)threadIdx.x;
+    const bool interior = v0 - 2 >= lo && v0 + (int64_t)kChunk16 + 2 <= hi;
+    if (!interior) {
+        // threads wholly outside the input count nothing; a warp wholly
+        // outside skips the chunk body
+        const bool outside = vt + 16 <= lo || vt >= hi;
+        st.skip = __all_sync(kFull, outside);
+        if (st.skip) {
+            st.vmask = 0;
+            st.slow = st.sur = st.only12 = false;
+            return 0;
+        }
+        if (outside) {
 #pragma unroll
-        for (int j = 0; j < 10; j++) w[j] = 0;
-        st.vmask = 0;
-        masked = true;
-    } else if (vt < lo || vt + 16 > hi) {   // straddles an end of the input
-        edge = masked = true;
-        st.vmask = 0;
+            for (int j = 0; j < 10; j++) w[j] = 0;
+            st.vmask = 0;
+            masked = true;
+        } else if (vt < lo || vt + 16 > hi) {   // straddles an end of the input
+            edge = masked = true;
+            st.vmask = 0;
 #pragma unroll
-        for (int i = 0; i < 16; i++)
-            if (vt + i >= lo && vt + i < hi) st.vmask |= 1u << i;
+            for (int i = 0; i < 16; i++)
+                if (vt + i >= lo && vt + i < hi) st.vmask |= 1u << i;
 #pragma unroll
-        for (int j = 0; j < 8; j++)
-            w[1 + j] &= unit_keep(vt + 2 * j, lo, hi) | (unit_keep(vt + 2 * j + 1, lo, hi) << 16);
+            for (int j = 0; j < 8; j++)
+                w[1 + j] &= unit_keep(vt + 2 * j, lo, hi) | (unit_keep(vt + 2 * j + 1, lo, hi) << 16);
+        }
+        if (!outside && (vt - 2 < lo || vt + 18 > hi)) {
+            w[0] &= unit_keep(vt - 2, lo, hi) | (unit_keep(vt - 1, lo, hi) << 16);
+            w[9] &= unit_keep(vt + 16, lo, hi) | (unit_keep(vt + 17, lo, hi) << 16);
+        }
+    } else {
+        st.skip = false;
     }
-    if (!outside && (vt - 2 < lo || vt + 18 > hi)) {
-        w[0] &= unit_keep(vt - 2, lo, hi) | (unit_keep(vt - 1, lo, hi) << 16);
-        w[9] &= unit_keep(vt + 16, lo, hi) | (unit_keep(vt + 17, lo, hi) << 16);
-    }
+    // some thread of the warp counts only part of its words (warp-uniform)
+    const bool wmasked = !interior && __any_sync(kFull, masked);
     if (kBE) {   // UTF-16BE: swap the bytes of every word once, then as UTF-16LE
 #pragma unroll
         for (int j = 0; j < 10; j++) w[j] = prmt(w[j], 0, 0x2301);
     }
+    // per word: 1 + [>=80] + [>=800] - [surrogate]: 1-3 bytes, 2 for either
+    // half of a pair
     uint32_t cnt = 0, any800 = 0, anysur = 0;
+    if (!wmasked) {
+        cnt = 16;
 #pragma unroll
-    for (int j = 0; j < 8; j++) {
-        const uint32_t x = w[1 + j];
-        const uint32_t ga = ge80_lanes(x), gb = ge800_lanes(x), s = surr_lanes(x);
-        uint32_t vm = 0x80008000u;
-        if (masked)
-            vm = (((st.vmask >> (2 * j)) & 1u) << 15) | (((st.vmask >> (2 * j + 1)) & 1u) << 31);
-        // 1 + [>=80] + [>=800] - [surrogate]: 1-3 bytes, 2 for either half of a pair
-        cnt += __popc(vm) + __popc(ga & vm) + __popc(gb & vm) - __popc(s & vm);
-        any800 |= gb;
-        anysur |= s;
+        for (int j = 0; j < 8; j++) {
+            const uint32_t x = w[1 + j];
+            const uint32_t ga = ge80_lanes(x), gb = ge800_lanes(x), s = surr_lanes(x);
+            cnt += __popc(ga) + __popc(gb) - __popc(s);
+            any800 |= gb;
+            anysur |= s;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const uint32_t x = w[1 + j];
+            const uint32_t ga = ge80_lanes(x), gb = ge800_lanes(x), s = surr_lanes(x);
+            const uint32_t vm = (((st.vmask >> (2 * j)) & 1u) << 15) | (((st.vmask >> (2 * j + 1)) & 1u) << 31);
+            cnt += __popc(vm) + __popc(ga & vm) + __popc(gb & vm) - __popc(s & vm);
+            any800 |= gb;
+            anysur |= s;
+        }
     }
     st.sur = __any_sync(kFull, anysur != 0);
     st.only12 = !__any_sync(kFull, any800 != 0);

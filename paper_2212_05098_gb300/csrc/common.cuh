@@ -194,15 +194,17 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *w
     }
     if (lane == 31) warp_tot[warp] = inc;
     cw_sync();
-    uint32_t base = 0, sum = 0;
+    // the warp totals, scanned across lanes 0 .. kWarps-1
+    constexpr int kWarps = kThreads / 32;
+    uint32_t t = lane < kWarps ? warp_tot[lane] : 0u;
 #pragma unroll
-    for (int w = 0; w < kThreads / 32; w++) {
-        const uint32_t t = warp_tot[w];
-        base += w < warp ? t : 0u;
-        sum += t;
+    for (int o = 1; o < kWarps; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(kFull, t, o);
+        if (lane >= o) t += u;
     }
-    *total = sum;
-    return base + inc - v;
+    *total = __shfl_sync(kFull, t, kWarps - 1);
+    const uint32_t below = __shfl_sync(kFull, t, warp > 0 ? warp - 1 : 0);
+    return (warp > 0 ? below : 0u) + inc - v;
 }
 
 // Decoupled look-back, run by one full warp for the item chunk `k` (k > 0)
@@ -272,6 +274,25 @@ __device__ __forceinline__ uint64_t lookback(const unsigned long long *status, u
     }
 }
 
+// The aligned middle part of block_store_bytes for a source offset of Q
+// words (and `sh` bits) into each 16-byte block: a separate loop per Q, so
+// the words are picked without selects.
+template <int Q>
+__device__ __forceinline__ void store_blocks(const uint4 *sv, uint8_t *d0, uint32_t nblk,
+                                             uint32_t sh)
+{
+    for (uint32_t b = threadIdx.x; b < nblk; b += kThreads) {
+        const uint4 A = sv[b], B = sv[b + 1];                       // bytes 16b .. 16b+31
+        const uint32_t x[8] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w};
+        uint4 v;
+        v.x = __funnelshift_r(x[Q], x[Q + 1], sh);
+        v.y = __funnelshift_r(x[Q + 1], x[Q + 2], sh);
+        v.z = __funnelshift_r(x[Q + 2], x[Q + 3], sh);
+        v.w = __funnelshift_r(x[Q + 3], x[Q + 4], sh);
+        *reinterpret_cast<uint4 *>(d0 + 16u * b) = v;
+    }
+}
+
 // Copy nbytes from shared memory (16-byte aligned, readable 32 bytes past the
 // end) to global dst with 16-byte aligned vector stores for the body and byte
 // stores at the two unaligned edges. Each thread reads two aligned 16-byte
@@ -287,23 +308,14 @@ __device__ __forceinline__ void block_store_bytes(const uint8_t *s_src, uint8_t 
     if (head > nbytes) head = nbytes;
     if (tid < head) dst[tid] = s_src[tid];
     const uint32_t nblk = (nbytes - head) >> 4;
-    const uint32_t q = (head >> 2) & 3u, sh = (head & 3u) * 8u;   // same for every block
+    const uint32_t sh = (head & 3u) * 8u;                      // same for every block
     const uint4 *sv = reinterpret_cast<const uint4 *>(s_src);
-    for (uint32_t b = tid; b < nblk; b += kThreads) {
-        const uint4 A = sv[b], B = sv[b + 1];                       // bytes 16b .. 16b+31
-        uint32_t x0, x1, x2, x3, x4;
-        switch (q) {
-        case 0: x0 = A.x; x1 = A.y; x2 = A.z; x3 = A.w; x4 = B.x; break;
-        case 1: x0 = A.y; x1 = A.z; x2 = A.w; x3 = B.x; x4 = B.y; break;
-        case 2: x0 = A.z; x1 = A.w; x2 = B.x; x3 = B.y; x4 = B.z; break;
-        default: x0 = A.w; x1 = B.x; x2 = B.y; x3 = B.z; x4 = B.w; break;
-        }
-        uint4 v;
-        v.x = __funnelshift_r(x0, x1, sh);
-        v.y = __funnelshift_r(x1, x2, sh);
-        v.z = __funnelshift_r(x2, x3, sh);
-        v.w = __funnelshift_r(x3, x4, sh);
-        *reinterpret_cast<uint4 *>(dst + head + 16u * b) = v;
+    uint8_t *d0 = dst + head;
+    switch ((head >> 2) & 3u) {
+    case 0: store_blocks<0>(sv, d0, nblk, sh); break;
+    case 1: store_blocks<1>(sv, d0, nblk, sh); break;
+    case 2: store_blocks<2>(sv, d0, nblk, sh); break;
+    default: store_blocks<3>(sv, d0, nblk, sh); break;
     }
     const uint32_t tail0 = head + 16u * nblk;
     if (tid < nbytes - tail0) dst[tail0 + tid] = s_src[tail0 + tid];

@@ -299,46 +299,37 @@ __device__ __forceinline__ uint32_t chunk8_phase1(St8 &st, const uint8_t *stage,
 }
 
 // Exact first error (flagged threads) and staging of the units.
-template <bool kWrite, bool kBE>
-__device__ __forceinline__ void chunk8_phase2(St8 &st, const uint8_t *stage, uint8_t *obuf,
-                                              uint32_t t_off, int64_t vt, int64_t lo, int64_t hi,
-                                              unsigned long long *s_err)
+// Units at the end positions (Eq. W_sum, W_out), four positions at a time
+// on two registers of 16-bit lanes, stored at p in order. k3 / k4: the warp
+// holds 3- or 4-byte leads (4-byte leads are also >= E0, so k4 implies k3).
+template <bool k3, bool k4, bool kBE>
+__device__ __forceinline__ void assemble8(const St8 &st, uint16_t *p)
 {
-    if (st.skip) return;
-    // Threads straddling an end of the input see the bytes outside it as
-    // zeros (ASCII), which neither create nor hide an error inside it, so
-    // the fast check covers them as well.
-    if (st.bad) {
-        const uint64_t key = first_error_exact8(stage, vt, lo, hi, t_off);
-        if (key != ~0ull) atomicMin(s_err, key);
-    }
-    if (!kWrite) return;
     const uint32_t *w = st.w;
     uint32_t s[9], c3[9], c4[9];
 #pragma unroll
     for (int j = 0; j < 9; j++) {
         // >= E0 / >= F0 at bit 7 of each byte (the other bits are not
         // used: the masks below replicate bit 7)
-        c3[j] = w[j] & (w[j] << 1) & (w[j] << 2);
-        c4[j] = c3[j] & (w[j] << 3);
+        if (k3) c3[j] = w[j] & (w[j] << 1) & (w[j] << 2);
+        if (k4) c4[j] = c3[j] & (w[j] << 3);
         const uint32_t na = prmt(w[j], 0, 0xBA98);        // 0xFF where byte >= 0x80
         s[j] = w[j] & ~(na & 0xC0C0C0C0u);                // tag bits stripped
     }
-    uint16_t *p = reinterpret_cast<uint16_t *>(obuf) + t_off;
 #pragma unroll
     for (int j = 1; j <= 8; j++) {
         const uint32_t na = prmt(w[j], 0, 0xBA98);
         const uint32_t s1 = back(s[j - 1], s[j], 8) & na;          // W_-1 where end byte is not ASCII
         uint32_t wa = prmt(s[j], 0, 0x4140) + (prmt(s1, 0, 0x4140) << 6);
         uint32_t wb = prmt(s[j], 0, 0x4342) + (prmt(s1, 0, 0x4342) << 6);
-        if (st.warp3) {
+        if (k3) {
             // W_-2 (low 4 bits) where the byte two back is a 3/4-byte lead
             const uint32_t m3 = prmt(c3[j - 1], c3[j], 0xDCBA);
             const uint32_t s2 = back(s[j - 1], s[j], 16) & m3 & 0x0F0F0F0Fu;
             wa += prmt(s2, 0, 0x4140) << 12;
             wb += prmt(s2, 0, 0x4342) << 12;
         }
-        if (st.warp4) {
+        if (k4) {
             // surrogates: high at the third byte of a 4-byte sequence,
             // low at its fourth byte (Eq. W_out)
             const uint32_t hma = prmt(c4[j - 1], c4[j], 0xBBAA);
@@ -360,6 +351,30 @@ __device__ __forceinline__ void chunk8_phase2(St8 &st, const uint8_t *stage, uin
         if (e & 0x00800000u) *p++ = (uint16_t)wb;
         if (e & 0x80000000u) *p++ = (uint16_t)(wb >> 16);
     }
+}
+
+template <bool kWrite, bool kBE>
+__device__ __forceinline__ void chunk8_phase2(St8 &st, const uint8_t *stage, uint8_t *obuf,
+                                              uint32_t t_off, int64_t vt, int64_t lo, int64_t hi,
+                                              unsigned long long *s_err)
+{
+    if (st.skip) return;
+    // Threads straddling an end of the input see the bytes outside it as
+    // zeros (ASCII), which neither create nor hide an error inside it, so
+    // the fast check covers them as well.
+    if (st.bad) {
+        const uint64_t key = first_error_exact8(stage, vt, lo, hi, t_off);
+        if (key != ~0ull) atomicMin(s_err, key);
+    }
+    if (!kWrite) return;
+    // the 3/4-byte parts only in warps that hold such leads (warp-uniform)
+    uint16_t *p = reinterpret_cast<uint16_t *>(obuf) + t_off;
+    if (st.warp4)
+        assemble8<true, true, kBE>(st, p);
+    else if (st.warp3)
+        assemble8<true, false, kBE>(st, p);
+    else
+        assemble8<false, false, kBE>(st, p);
 }
 
 // ===========================================================================

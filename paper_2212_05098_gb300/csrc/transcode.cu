@@ -173,6 +173,56 @@ struct St8 {
     bool warp3, warp4;
 };
 
+// Structure check (expected continuations = continuations), C0/C1 check
+// and end positions of one thread (Sec. 6.1, 6.4); returns its unit count.
+// k3: the warp holds >= E0 leads (else every >= E0 / >= F0 term is zero and
+// dropped). ORs its >= F0 leads into any4.
+template <bool k3>
+__device__ __forceinline__ uint32_t structure8(St8 &st, const uint32_t *w, bool wmasked,
+                                               uint32_t &bad, uint32_t &any4)
+{
+    Cls cl[10];
+#pragma unroll
+    for (int j = 0; j < 10; j++) {
+        cl[j] = classify(w[j]);
+        if (!k3) cl[j].c3 = cl[j].c4 = 0;
+    }
+    // leads in the look-behind word shape the units at the first positions
+    any4 = cl[0].c4;
+    uint32_t ec[9], cnt = 0;
+#pragma unroll
+    for (int j = 1; j <= 8; j++) {
+        const uint32_t exp = back(cl[j - 1].c2, cl[j].c2, 8) | back(cl[j - 1].c3, cl[j].c3, 16) |
+                             back(cl[j - 1].c4, cl[j].c4, 24);
+        bad |= exp ^ cl[j].ct;
+        ec[j - 1] = exp & cl[j].ct;
+        // C0 / C1: 2-byte leads whose bits 4..1 are zero
+        bad |= cl[j].c2 & ~cl[j].c3 & zero_bytes(w[j] & 0x1E1E1E1Eu);
+        any4 |= cl[j].c4;
+    }
+    // continuations the last leads expect at positions 32..34
+    const uint32_t exp9 = (cl[8].c2 >> 24) | (cl[8].c3 >> 16) | (cl[8].c4 >> 8);
+    bad |= exp9 & ~cl[9].ct;
+    ec[8] = exp9 & cl[9].ct;
+    if (!wmasked) {
+#pragma unroll
+        for (int j = 1; j <= 8; j++) {
+            const uint32_t e = (~ahead(ec[j - 1], ec[j], 8) | back(cl[j - 1].c4, cl[j].c4, 16)) & kB7;
+            st.end[j - 1] = e;
+            cnt += __popc(e);
+        }
+    } else {
+#pragma unroll
+        for (int j = 1; j <= 8; j++) {
+            uint32_t e = (~ahead(ec[j - 1], ec[j], 8) | back(cl[j - 1].c4, cl[j].c4, 16)) & kB7;
+            e &= spread4((st.vmask >> (4 * (j - 1))) & 0xFu);
+            st.end[j - 1] = e;
+            cnt += __popc(e);
+        }
+    }
+    return cnt;
+}
+
 // Load, classify, check structure, count units. Returns the thread's count.
 __device__ __forceinline__ uint32_t chunk8_phase1(St8 &st, const uint8_t *stage, int64_t vt,
                                                   int64_t lo, int64_t hi)
@@ -228,49 +278,20 @@ __device__ __forceinline__ uint32_t chunk8_phase1(St8 &st, const uint8_t *stage,
     // unmasked warps branch around that work instead of predicating it)
     const bool wmasked = !interior && __any_sync(kFull, masked);
 
-    uint32_t bad = 0, any3, any4, cnt = 0;
-    {
-        Cls cl[10];
+    // leads >= E0 (3/4-byte) anywhere in the warp, the look-behind word
+    // included: without them the phase below drops their terms
+    uint32_t any3 = 0;
 #pragma unroll
-        for (int j = 0; j < 10; j++) cl[j] = classify(w[j]);
-        // leads in the look-behind word shape the units at the first positions
-        any3 = cl[0].c3;
-        any4 = cl[0].c4;
-        uint32_t ec[9];
-#pragma unroll
-        for (int j = 1; j <= 8; j++) {
-            const uint32_t exp = back(cl[j - 1].c2, cl[j].c2, 8) | back(cl[j - 1].c3, cl[j].c3, 16) |
-                                 back(cl[j - 1].c4, cl[j].c4, 24);
-            bad |= exp ^ cl[j].ct;
-            ec[j - 1] = exp & cl[j].ct;
-            // C0 / C1: 2-byte leads whose bits 4..1 are zero
-            bad |= cl[j].c2 & ~cl[j].c3 & zero_bytes(w[j] & 0x1E1E1E1Eu);
-            any3 |= cl[j].c3;
-            any4 |= cl[j].c4;
-        }
-        // continuations the last leads expect at positions 32..34
-        const uint32_t exp9 = (cl[8].c2 >> 24) | (cl[8].c3 >> 16) | (cl[8].c4 >> 8);
-        bad |= exp9 & ~cl[9].ct;
-        ec[8] = exp9 & cl[9].ct;
-        if (!wmasked) {
-#pragma unroll
-            for (int j = 1; j <= 8; j++) {
-                const uint32_t e = (~ahead(ec[j - 1], ec[j], 8) | back(cl[j - 1].c4, cl[j].c4, 16)) & kB7;
-                st.end[j - 1] = e;
-                cnt += __popc(e);
-            }
-        } else {
-#pragma unroll
-            for (int j = 1; j <= 8; j++) {
-                uint32_t e = (~ahead(ec[j - 1], ec[j], 8) | back(cl[j - 1].c4, cl[j].c4, 16)) & kB7;
-                e &= spread4((st.vmask >> (4 * (j - 1))) & 0xFu);
-                st.end[j - 1] = e;
-                cnt += __popc(e);
-            }
-        }
+    for (int j = 0; j < 9; j++) any3 |= w[j] & (w[j] << 1) & (w[j] << 2);
+    st.warp3 = __any_sync(kFull, (any3 & kB7) != 0);
+    uint32_t bad = 0, any4 = 0, cnt;
+    if (st.warp3) {
+        cnt = structure8<true>(st, w, wmasked, bad, any4);
+        st.warp4 = __any_sync(kFull, any4 != 0);
+    } else {
+        cnt = structure8<false>(st, w, wmasked, bad, any4);
+        st.warp4 = false;
     }
-    st.warp3 = __any_sync(kFull, any3 != 0);
-    st.warp4 = __any_sync(kFull, any4 != 0);
     if (st.warp3) {
         // E0 + 80..9F (overlong), ED + A0..BF (surrogate): a byte that is E0
         // when bit 5 of the next byte is clear, or ED when it is set
@@ -501,17 +522,26 @@ __device__ __forceinline__ uint32_t chunk16_phase1(St16 &st, const uint8_t *stag
 #pragma unroll
         for (int j = 0; j < 10; j++) w[j] = prmt(w[j], 0, 0x2301);
     }
+    // does the warp hold words of U+0800 and above? (warp-uniform; words
+    // outside the input are zero)
+    uint32_t top5 = 0;
+#pragma unroll
+    for (int j = 0; j < 8; j++) top5 |= w[1 + j] & 0xF800F800u;
+    st.only12 = !__any_sync(kFull, top5 != 0);
     // per word: 1 + [>=80] + [>=800] - [surrogate]: 1-3 bytes, 2 for either
     // half of a pair
-    uint32_t cnt = 0, any800 = 0, anysur = 0;
-    if (!wmasked) {
+    uint32_t cnt = 0, anysur = 0;
+    if (!wmasked && st.only12) {
+        cnt = 16;
+#pragma unroll
+        for (int j = 0; j < 8; j++) cnt += __popc(ge80_lanes(w[1 + j]));
+    } else if (!wmasked) {
         cnt = 16;
 #pragma unroll
         for (int j = 0; j < 8; j++) {
             const uint32_t x = w[1 + j];
             const uint32_t ga = ge80_lanes(x), gb = ge800_lanes(x), s = surr_lanes(x);
             cnt += __popc(ga) + __popc(gb) - __popc(s);
-            any800 |= gb;
             anysur |= s;
         }
     } else {
@@ -521,12 +551,10 @@ __device__ __forceinline__ uint32_t chunk16_phase1(St16 &st, const uint8_t *stag
             const uint32_t ga = ge80_lanes(x), gb = ge800_lanes(x), s = surr_lanes(x);
             const uint32_t vm = (((st.vmask >> (2 * j)) & 1u) << 15) | (((st.vmask >> (2 * j + 1)) & 1u) << 31);
             cnt += __popc(vm) + __popc(ga & vm) + __popc(gb & vm) - __popc(s & vm);
-            any800 |= gb;
             anysur |= s;
         }
     }
     st.sur = __any_sync(kFull, anysur != 0);
-    st.only12 = !__any_sync(kFull, any800 != 0);
     st.slow = edge;
     return cnt;
 }

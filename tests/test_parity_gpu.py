@@ -222,3 +222,42 @@ def test_utf16be_both_directions(ctx, profile):
         check_u16_be(ctx, bad.view(np.uint8))
     check_u8_be(ctx, big8.data, cap_units=100)
     check_u16_be(ctx, be16, cap_bytes=333)
+
+
+def _patchwork(seed: int, n_runs: int = 300):
+    """Code points in runs of a few hundred bytes, each run from one text
+    class (ASCII only, or one profile), so that neighbouring warps of a chunk
+    see different classes of text and pick different paths."""
+    rng = np.random.Generator(np.random.Philox(key=seed))
+    profiles = ["latin", "cyrillic", "cjk", "emoji", "mix"]
+    parts = []
+    for i in range(n_runs):
+        nbytes = int(rng.integers(40, 2600))
+        k = int(rng.integers(len(profiles) + 1))
+        if k == len(profiles):
+            parts.append(rng.integers(0x20, 0x7F, size=nbytes).astype(np.uint32))
+        else:
+            parts.append(textgen.generate(profiles[k], nbytes, textgen.UTF8,
+                                          seed=seed * 1000 + i).cps)
+    return np.concatenate(parts)
+
+
+@pytest.mark.parametrize("seed", [71, 72, 73])
+def test_mixed_classes_per_warp(ctx, seed):
+    """Text whose class changes every few hundred bytes, valid and with one
+    injected error, in both directions: the per-warp paths (ASCII / 2-byte /
+    3-byte / 4-byte leads, 1-2-byte / BMP / surrogate UTF-16) meet at
+    arbitrary positions inside chunks and threads."""
+    cps = _patchwork(seed)
+    d8 = textgen.encode(cps, textgen.UTF8).copy()
+    d16 = textgen.encode(cps, textgen.UTF16).copy()
+    check_u8(ctx, d8)
+    check_u16(ctx, d16)
+    rng = np.random.Generator(np.random.Philox(key=seed + 100))
+    for i in range(6):
+        bad8 = d8.copy()
+        bad8[int(rng.integers(bad8.size))] = [0xFF, 0x80, 0xC0, 0xED][i % 4]
+        check_u8(ctx, bad8[: bad8.size - 13 * i])
+        words = d16.copy().view("<u2")
+        words[int(rng.integers(words.size))] = [0xD800, 0xDC00, 0xDBFF][i % 3]
+        check_u16(ctx, words.view(np.uint8)[: d16.size - 26 * i])

@@ -467,17 +467,26 @@ static gbu_result run_host(gbu_ctx *c, Op op, const void *h_in, uint64_t n, void
     if (ensure_scratch(c, (16 + max_units * uin + kChunkBytes - 1) / kChunkBytes + 1, s) != GBU_OK)
         return make(GBU_DEVICE_ERROR);
     if (!ok(cudaStreamSynchronize(s))) return make(GBU_DEVICE_ERROR);
+    // Every return below first waits for all three streams: no copy may
+    // still read the caller's input or write its output after the call.
+    auto drain = [&]() {
+        cudaStreamSynchronize(c->h2d);
+        cudaStreamSynchronize(s);
+        cudaStreamSynchronize(c->d2h);
+    };
     // copy-in and kernels for every slice
     for (int k = 0; k < ns; k++) {
         const uint64_t u0 = cuts[k], nu = cuts[k + 1] - cuts[k];
         if (!ok(cudaMemcpyAsync(c->io + u0 * uin, hb + u0 * uin, nu * uin, cudaMemcpyHostToDevice,
                                 c->h2d)) ||
-            !ok(cudaEventRecord(c->ev_in[k], c->h2d)) || !ok(cudaStreamWaitEvent(s, c->ev_in[k], 0)))
+            !ok(cudaEventRecord(c->ev_in[k], c->h2d)) || !ok(cudaStreamWaitEvent(s, c->ev_in[k], 0))) {
+            drain();
             return make(GBU_DEVICE_ERROR);
+        }
         const int32_t st = enqueue(c, op, c->io + u0 * uin, nu, c->io + out_base[k], nu * per_unit,
                                    true, reinterpret_cast<ResultSlot *>(c->d_slice_res + k), s);
         if (st != GBU_OK || !ok(cudaEventRecord(c->ev_done[k], s))) {
-            cudaStreamSynchronize(s);
+            drain();
             return make(st != GBU_OK ? st : GBU_DEVICE_ERROR);
         }
     }
@@ -485,20 +494,24 @@ static gbu_result run_host(gbu_ctx *c, Op op, const void *h_in, uint64_t n, void
     uint64_t out_off = 0;
     gbu_result total = make(GBU_OK, n, 0);
     for (int k = 0; k < ns; k++) {
-        if (!ok(cudaEventSynchronize(c->ev_done[k]))) return make(GBU_DEVICE_ERROR);
+        if (!ok(cudaEventSynchronize(c->ev_done[k]))) {
+            drain();
+            return make(GBU_DEVICE_ERROR);
+        }
         gbu_result r;
         std::memcpy(&r, const_cast<const gbu_result *>(c->h_slice_res + k), sizeof r);
         if (r.status >= GBU_INVALID_ARG) {
-            cudaStreamSynchronize(s);
-            cudaStreamSynchronize(c->d2h);
+            drain();
             if (r.status == GBU_DEVICE_TIMEOUT || r.status == GBU_DEVICE_ERROR) c->dirty = true;
             return r;
         }
         const uint64_t keep = out_off < cap ? std::min<uint64_t>(r.out_len, cap - out_off) : 0;
         if (keep && !ok(cudaMemcpyAsync(static_cast<uint8_t *>(h_out) + out_off * ub,
                                         c->io + out_base[k], keep * ub, cudaMemcpyDeviceToHost,
-                                        c->d2h)))
+                                        c->d2h))) {
+            drain();
             return make(GBU_DEVICE_ERROR);
+        }
         if (r.status != GBU_OK) {   // an encoding error ends the input
             total = make(r.status, cuts[k] + r.in_offset, out_off + r.out_len);
             break;
@@ -506,7 +519,8 @@ static gbu_result run_host(gbu_ctx *c, Op op, const void *h_in, uint64_t n, void
         out_off += r.out_len;
         total.out_len = out_off;
     }
-    if (!ok(cudaStreamSynchronize(s)) || !ok(cudaStreamSynchronize(c->d2h)))
+    if (!ok(cudaStreamSynchronize(c->h2d)) || !ok(cudaStreamSynchronize(s)) ||
+        !ok(cudaStreamSynchronize(c->d2h)))
         return make(GBU_DEVICE_ERROR);
     if (total.status == GBU_OK && total.out_len > cap) total.status = GBU_OUTPUT_TOO_SMALL;
     return total;

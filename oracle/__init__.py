@@ -1,4 +1,5 @@
-"""Oracle: scalar CPU UTF-8 <-> UTF-16LE transcoder (test infrastructure only).
+"""Oracle: scalar CPU UTF-8 <-> UTF-16LE (and UTF-8 <-> UTF-32LE) transcoder
+(test infrastructure only).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
 ``--impl reference`` legs of ``bench.py`` may import this package. The product
@@ -12,7 +13,9 @@ Sec. 7.5. The C source (``oracle.c``) states the readings taken where the
 paper is silent (error kinds and their precedence, capacity handling).
 
 Arrays are numpy ``uint8`` buffers; UTF-16LE data is passed as bytes
-(``2 * n_units``), low byte first.
+(``2 * n_units``), low byte first, UTF-32LE data likewise (``4 * n_units``).
+UTF-32 units above U+10FFFF are TOO_LARGE and units in D800-DFFF SURROGATE
+(the library's convention; Sec. 2 defines UTF-32 as the code point itself).
 """
 from __future__ import annotations
 
@@ -70,11 +73,13 @@ def _load():
         lib = ctypes.CDLL(path)
         u8p = ctypes.POINTER(ctypes.c_uint8)
         rp = ctypes.POINTER(_CResult)
-        for name in ("oracle_utf8_to_utf16le", "oracle_utf16le_to_utf8"):
+        for name in ("oracle_utf8_to_utf16le", "oracle_utf16le_to_utf8",
+                     "oracle_utf8_to_utf32le", "oracle_utf32le_to_utf8"):
             f = getattr(lib, name)
             f.argtypes = [u8p, ctypes.c_uint64, u8p, ctypes.c_uint64, rp]
             f.restype = None
-        for name in ("oracle_utf16_length_from_utf8", "oracle_utf8_length_from_utf16le"):
+        for name in ("oracle_utf16_length_from_utf8", "oracle_utf8_length_from_utf16le",
+                     "oracle_utf32_length_from_utf8", "oracle_utf8_length_from_utf32le"):
             f = getattr(lib, name)
             f.argtypes = [u8p, ctypes.c_uint64, rp]
             f.restype = None
@@ -169,3 +174,55 @@ def utf8_length_from_utf16be(data) -> Result:
 
 def library_path() -> str:
     return os.path.abspath(_build.build())
+
+
+# ---- UTF-32LE (Sec. 2: one 32-bit unit per code point) ---------------------
+
+def utf8_to_utf32le(data, cap_units: int | None = None):
+    """Transcode UTF-8 bytes; returns (Result, uint32 array of length min(out_len, cap))."""
+    lib = _load()
+    src = _as_u8(data)
+    n = src.size
+    if cap_units is None:
+        cap_units = n  # worst case: one unit per input byte
+    out = np.zeros(max(cap_units, 1) * 4, dtype=np.uint8)
+    r = _CResult()
+    lib.oracle_utf8_to_utf32le(_ptr(src), n, _ptr(out), cap_units, ctypes.byref(r))
+    res = Result(r.status, r.in_offset, r.out_len)
+    keep = min(res.out_len, cap_units)
+    return res, out[: 4 * keep].view("<u4").copy()
+
+
+def utf32le_to_utf8(data, cap_bytes: int | None = None):
+    """Transcode UTF-32LE (uint32 array or LE bytes); returns (Result, uint8 array)."""
+    lib = _load()
+    src = _as_u8(data)
+    if src.size % 4:
+        raise ValueError("UTF-32LE input must have a multiple of 4 bytes")
+    n = src.size // 4
+    if cap_bytes is None:
+        cap_bytes = 4 * n  # worst case: four bytes per input unit
+    out = np.zeros(max(cap_bytes, 1), dtype=np.uint8)
+    r = _CResult()
+    lib.oracle_utf32le_to_utf8(_ptr(src), n, _ptr(out), cap_bytes, ctypes.byref(r))
+    res = Result(r.status, r.in_offset, r.out_len)
+    keep = min(res.out_len, cap_bytes)
+    return res, out[:keep].copy()
+
+
+def utf32_length_from_utf8(data) -> Result:
+    lib = _load()
+    src = _as_u8(data)
+    r = _CResult()
+    lib.oracle_utf32_length_from_utf8(_ptr(src), src.size, ctypes.byref(r))
+    return Result(r.status, r.in_offset, r.out_len)
+
+
+def utf8_length_from_utf32le(data) -> Result:
+    lib = _load()
+    src = _as_u8(data)
+    if src.size % 4:
+        raise ValueError("UTF-32LE input must have a multiple of 4 bytes")
+    r = _CResult()
+    lib.oracle_utf8_length_from_utf32le(_ptr(src), src.size // 4, ctypes.byref(r))
+    return Result(r.status, r.in_offset, r.out_len)

@@ -1,5 +1,6 @@
 /*
- * Oracle: plain, slow, obviously-correct scalar UTF-8 <-> UTF-16LE transcoder.
+ * Oracle: plain, slow, obviously-correct scalar UTF-8 <-> UTF-16LE transcoder
+ * (and UTF-8 <-> UTF-32LE, the third format of Sec. 2).
  *
  * TEST INFRASTRUCTURE ONLY. Nothing on the product path may link, load or call
  * this file; only the test-suite, the smoke check and the CPU-baseline leg of
@@ -205,6 +206,103 @@ static void u16_to_u8(const uint8_t *in, uint64_t n, uint8_t *out,
     finish(r, err, p, n, o, cap_bytes, check_cap);
 }
 
+/* ---- UTF-32LE ---------------------------------------------------------- */
+
+static void put32(uint8_t *out, uint64_t cap_units, uint64_t *o, uint32_t cp)
+{
+    /* One UTF-32LE unit: the code point itself, low byte first (Sec. 2). */
+    if (out && *o < cap_units) {
+        out[4 * *o] = (uint8_t)(cp & 0xFF);
+        out[4 * *o + 1] = (uint8_t)((cp >> 8) & 0xFF);
+        out[4 * *o + 2] = (uint8_t)((cp >> 16) & 0xFF);
+        out[4 * *o + 3] = (uint8_t)(cp >> 24);
+    }
+    (*o)++;
+}
+
+/*
+ * UTF-8 -> UTF-32LE: the same character-by-character decoding and the same
+ * validation as UTF-8 -> UTF-16LE above (Sec. 2.2, Table 1, Fig. 1(a),
+ * Sec. 6.4); every character becomes one 32-bit unit holding its code point.
+ */
+static void u8_to_u32(const uint8_t *in, uint64_t n, uint8_t *out,
+                      uint64_t cap_units, int check_cap, oracle_result *r)
+{
+    uint64_t p = 0, o = 0;
+    int32_t err = OR_OK;
+    while (p < n) {
+        uint8_t b = in[p];
+        uint32_t len, cp, k;
+        if (b <= 0x7F) {
+            put32(out, cap_units, &o, b);
+            p += 1;
+            continue;
+        }
+        if (b <= 0xBF) { err = OR_TOO_LONG; break; }
+        if (b <= 0xC1) { err = OR_OVERLONG; break; }
+        if (b <= 0xDF) len = 2;
+        else if (b <= 0xEF) len = 3;
+        else if (b <= 0xF4) len = 4;
+        else { err = OR_HEADER_BITS; break; }
+        if (n - p < len) { err = OR_TOO_SHORT; break; }
+        for (k = 1; k < len; k++)
+            if (!is_continuation(in[p + k])) break;
+        if (k < len) { err = OR_TOO_SHORT; break; }
+        if (len == 2) {
+            cp = ((uint32_t)(b & 0x1F) << 6) | (in[p + 1] & 0x3F);
+        } else if (len == 3) {
+            cp = ((uint32_t)(b & 0x0F) << 12) | ((uint32_t)(in[p + 1] & 0x3F) << 6)
+               | (in[p + 2] & 0x3F);
+        } else {
+            cp = ((uint32_t)(b & 0x07) << 18) | ((uint32_t)(in[p + 1] & 0x3F) << 12)
+               | ((uint32_t)(in[p + 2] & 0x3F) << 6) | (in[p + 3] & 0x3F);
+        }
+        if (len == 3 && cp < 0x800) { err = OR_OVERLONG; break; }
+        if (len == 3 && cp >= 0xD800 && cp <= 0xDFFF) { err = OR_SURROGATE; break; }
+        if (len == 4 && cp < 0x10000) { err = OR_OVERLONG; break; }
+        if (len == 4 && cp > 0x10FFFF) { err = OR_TOO_LARGE; break; }
+        put32(out, cap_units, &o, cp);
+        p += len;
+    }
+    finish(r, err, p, n, o, cap_units, check_cap);
+}
+
+/*
+ * UTF-32LE -> UTF-8, one unit at a time (Sec. 2: a UTF-32 unit is the code
+ * point). A unit above U+10FFFF is TOO_LARGE and one in D800-DFFF is
+ * SURROGATE (the library's convention, named like the UTF-8 value errors of
+ * Sec. 6.4, rules 5 and 6), at the unit's index. Bytes per Fig. 1(a).
+ */
+static void u32_to_u8(const uint8_t *in, uint64_t n, uint8_t *out,
+                      uint64_t cap_bytes, int check_cap, oracle_result *r)
+{
+    uint64_t p = 0, o = 0;
+    int32_t err = OR_OK;
+    while (p < n) {
+        uint32_t cp = (uint32_t)in[4 * p] | ((uint32_t)in[4 * p + 1] << 8)
+                    | ((uint32_t)in[4 * p + 2] << 16) | ((uint32_t)in[4 * p + 3] << 24);
+        if (cp > 0x10FFFF) { err = OR_TOO_LARGE; break; }
+        if (cp >= 0xD800 && cp <= 0xDFFF) { err = OR_SURROGATE; break; }
+        if (cp <= 0x7F) {
+            put8(out, cap_bytes, &o, cp);
+        } else if (cp <= 0x7FF) {
+            put8(out, cap_bytes, &o, 0xC0 | (cp >> 6));
+            put8(out, cap_bytes, &o, 0x80 | (cp & 0x3F));
+        } else if (cp <= 0xFFFF) {
+            put8(out, cap_bytes, &o, 0xE0 | (cp >> 12));
+            put8(out, cap_bytes, &o, 0x80 | ((cp >> 6) & 0x3F));
+            put8(out, cap_bytes, &o, 0x80 | (cp & 0x3F));
+        } else {
+            put8(out, cap_bytes, &o, 0xF0 | (cp >> 18));
+            put8(out, cap_bytes, &o, 0x80 | ((cp >> 12) & 0x3F));
+            put8(out, cap_bytes, &o, 0x80 | ((cp >> 6) & 0x3F));
+            put8(out, cap_bytes, &o, 0x80 | (cp & 0x3F));
+        }
+        p += 1;
+    }
+    finish(r, err, p, n, o, cap_bytes, check_cap);
+}
+
 /* ---- exported entry points (ctypes) ------------------------------------ */
 
 void oracle_utf8_to_utf16le(const uint8_t *in, uint64_t n_bytes, uint8_t *out,
@@ -228,4 +326,26 @@ void oracle_utf16_length_from_utf8(const uint8_t *in, uint64_t n_bytes, oracle_r
 void oracle_utf8_length_from_utf16le(const uint8_t *in, uint64_t n_units, oracle_result *r)
 {
     u16_to_u8(in, n_units, NULL, 0, 0, r);
+}
+
+void oracle_utf8_to_utf32le(const uint8_t *in, uint64_t n_bytes, uint8_t *out,
+                            uint64_t cap_units, oracle_result *r)
+{
+    u8_to_u32(in, n_bytes, out, cap_units, 1, r);
+}
+
+void oracle_utf32le_to_utf8(const uint8_t *in, uint64_t n_units, uint8_t *out,
+                            uint64_t cap_bytes, oracle_result *r)
+{
+    u32_to_u8(in, n_units, out, cap_bytes, 1, r);
+}
+
+void oracle_utf32_length_from_utf8(const uint8_t *in, uint64_t n_bytes, oracle_result *r)
+{
+    u8_to_u32(in, n_bytes, NULL, 0, 0, r);
+}
+
+void oracle_utf8_length_from_utf32le(const uint8_t *in, uint64_t n_units, oracle_result *r)
+{
+    u32_to_u8(in, n_units, NULL, 0, 0, r);
 }

@@ -277,3 +277,91 @@ def test_utf16be_matches_python_codecs():
     rb, _ = oracle.utf16be_to_utf8(be)
     assert (ra.status, ra.in_offset, ra.out_len) == (rb.status, rb.in_offset, rb.out_len)
     assert rb.status == oracle.LONE_HIGH_SURROGATE and rb.in_offset == 1
+
+
+# --- UTF-32LE (Sec. 2's third format) ----------------------------------------
+
+def test_utf32_all_scalars_match_python_codecs():
+    cps = _all_scalars()
+    s = cps.astype("<u4").tobytes().decode("utf-32-le")
+    u8 = s.encode("utf-8")
+    r, out = oracle.utf8_to_utf32le(u8)
+    assert r == oracle.Result(oracle.OK, len(u8), cps.size)
+    assert np.array_equal(out, cps.astype(np.uint32))
+    r, out = oracle.utf32le_to_utf8(cps.astype("<u4"))
+    assert r == oracle.Result(oracle.OK, cps.size, len(u8))
+    assert out.tobytes() == u8
+    assert oracle.utf32_length_from_utf8(u8) == oracle.Result(oracle.OK, len(u8), cps.size)
+    assert oracle.utf8_length_from_utf32le(cps.astype("<u4")) == \
+        oracle.Result(oracle.OK, cps.size, len(u8))
+
+
+def _py_utf32(data: bytes):
+    try:
+        return None, data.decode("utf-32-le")
+    except UnicodeDecodeError as e:
+        return e.start // 4, data[: e.start - e.start % 4].decode("utf-32-le")
+
+
+def test_utf32_invalid_units():
+    """Every surrogate value and values above U+10FFFF, alone and after a
+    valid prefix: SURROGATE / TOO_LARGE at the unit, prefix transcoded; the
+    position agrees with Python's UTF-32 decoder."""
+    prefix = np.array([0x41, 0xE9, 0x4E2D, 0x1F600], dtype="<u4")
+    plen = len("Aé中😀".encode("utf-8"))
+    bad = [(u, oracle.SURROGATE) for u in range(0xD800, 0xE000)] + \
+          [(u, oracle.TOO_LARGE) for u in (0x110000, 0x110001, 0x1FFFFF, 0x7FFFFFFF, 0x80000000,
+                                            0xFFFFFFFF, 0x00110000 + 12345)]
+    for u, kind in bad:
+        data = np.concatenate([prefix, np.array([u, 0x41], dtype="<u4")])
+        r, out = oracle.utf32le_to_utf8(data)
+        assert (r.status, r.in_offset, r.out_len) == (kind, 4, plen), hex(u)
+        assert out.tobytes() == "Aé中😀".encode("utf-8")
+        err, _ = _py_utf32(data.tobytes())
+        assert err == 4, hex(u)
+        assert oracle.utf8_length_from_utf32le(data) == r
+
+
+@pytest.mark.parametrize("profile", ["mix", "emoji"])
+def test_utf8_to_utf32_errors_match_utf16_and_python(profile):
+    """UTF-8 -> UTF-32 validates exactly like UTF-8 -> UTF-16 (same status and
+    offset); its prefix length counts code points (Python's decode of the
+    prefix)."""
+    base = textgen.generate(profile, 4096, textgen.UTF8, seed=17)
+    for i in range(60):
+        data = textgen.mutate(base.data, i % 4, seed=3000 + i)
+        cut = data[: 4096 - (i % 7)].tobytes()
+        r32, out32 = oracle.utf8_to_utf32le(cut)
+        r16, _ = oracle.utf8_to_utf16le(cut)
+        assert (r32.status, r32.in_offset) == (r16.status, r16.in_offset)
+        err, prefix = _py_utf8(cut)
+        assert r32.out_len == len(prefix)
+        assert np.array_equal(out32, np.frombuffer(prefix.encode("utf-32-le"), dtype="<u4"))
+        assert oracle.utf32_length_from_utf8(cut) == r32
+
+
+def test_utf32_random_units_against_python():
+    rng = np.random.Generator(np.random.Philox(key=91))
+    for i in range(200):
+        n = int(rng.integers(1, 64))
+        # mostly valid values, some surrogates and out-of-range ones
+        u = rng.integers(0, 0x110000, size=n).astype(np.uint32)
+        u[rng.random(n) < 0.02] = rng.integers(0xD800, 0xE000)
+        u[rng.random(n) < 0.02] = rng.integers(0x110000, 0xFFFFFFFF, dtype=np.uint64)
+        data = u.astype("<u4").tobytes()
+        r, out = oracle.utf32le_to_utf8(data)
+        err, prefix = _py_utf32(data)
+        if err is None:
+            assert (r.status, r.in_offset) == (oracle.OK, n)
+        else:
+            assert r.status in (oracle.SURROGATE, oracle.TOO_LARGE) and r.in_offset == err
+        assert out.tobytes() == prefix.encode("utf-8")
+
+
+def test_utf32_capacity():
+    data = np.array([0x41, 0x4E2D, 0x1F600], dtype="<u4")        # 1 + 3 + 4 bytes
+    r, out = oracle.utf32le_to_utf8(data, cap_bytes=5)
+    assert (r.status, r.in_offset, r.out_len) == (oracle.OUTPUT_TOO_SMALL, 3, 8)
+    r, out = oracle.utf8_to_utf32le("A中😀".encode(), cap_units=2)
+    assert (r.status, r.in_offset, r.out_len) == (oracle.OUTPUT_TOO_SMALL, 8, 3)
+    assert out.tolist() == [0x41, 0x4E2D]

@@ -131,6 +131,33 @@ int32_t gbu_utf16be_to_utf8_async(gbu_ctx *ctx, const uint16_t *d_in, uint64_t n
                                   uint8_t *d_out, uint64_t cap_bytes, gbu_result *result,
                                   void *stream);
 
+/* UTF-32LE forms (Sec. 2: a UTF-32 unit is the code point itself, little-
+ * endian 32-bit words; UTF-8 bytes per Fig. 1(a)). Synchronous; results as
+ * for the UTF-16 calls, with units of 32-bit words on the UTF-32 side.
+ *
+ * gbu_utf8_to_utf32le: d_in any alignment; d_out 4-byte aligned, cap_units
+ *   32-bit units (n_bytes is never too small). The UTF-8 is validated by the
+ *   rules of Sec. 6.4 exactly as by gbu_utf8_to_utf16le (same status and
+ *   in_offset); out_len counts code points.
+ * gbu_utf32le_to_utf8: d_in 4-byte aligned, n_units 32-bit units; d_out any
+ *   alignment, cap_bytes bytes (4 * n_units is never too small). A unit above
+ *   U+10FFFF is GBU_TOO_LARGE and one in D800-DFFF is GBU_SURROGATE, at its
+ *   index (the library's convention; the paper defines no UTF-32 errors).
+ * Length-only and validation calls as for UTF-16. A misaligned pointer is
+ * GBU_INVALID_ARG. Each call runs short launches on `stream` (the UTF-8 side
+ * first runs the UTF-8 validation) and waits for them; workspace is the
+ * context's. */
+gbu_result gbu_utf8_to_utf32le(gbu_ctx *ctx, const uint8_t *d_in, uint64_t n_bytes,
+                               uint32_t *d_out, uint64_t cap_units, void *stream);
+gbu_result gbu_utf32le_to_utf8(gbu_ctx *ctx, const uint32_t *d_in, uint64_t n_units,
+                               uint8_t *d_out, uint64_t cap_bytes, void *stream);
+gbu_result gbu_utf32_length_from_utf8(gbu_ctx *ctx, const uint8_t *d_in, uint64_t n_bytes,
+                                      void *stream);
+gbu_result gbu_utf8_length_from_utf32le(gbu_ctx *ctx, const uint32_t *d_in, uint64_t n_units,
+                                        void *stream);
+gbu_result gbu_validate_utf32le(gbu_ctx *ctx, const uint32_t *d_in, uint64_t n_units,
+                                void *stream);
+
 /* Validation only (the paper's validation, Sec. 6.4 and 7.4, without the
  * transcoding): status and in_offset as for the transcoding calls (the
  * first invalid unit), out_len always 0. No output offsets are computed, so

@@ -104,6 +104,11 @@ SIGNATURES = {
     "gbu_utf16be_to_utf8": (gbu_result, [_VP, _VP, _U64, _VP, _U64, _VP]),
     "gbu_utf8_length_from_utf16be": (gbu_result, [_VP, _VP, _U64, _VP]),
     "gbu_validate_utf16be": (gbu_result, [_VP, _VP, _U64, _VP]),
+    "gbu_utf8_to_utf32le": (gbu_result, [_VP, _VP, _U64, _VP, _U64, _VP]),
+    "gbu_utf32le_to_utf8": (gbu_result, [_VP, _VP, _U64, _VP, _U64, _VP]),
+    "gbu_utf32_length_from_utf8": (gbu_result, [_VP, _VP, _U64, _VP]),
+    "gbu_utf8_length_from_utf32le": (gbu_result, [_VP, _VP, _U64, _VP]),
+    "gbu_validate_utf32le": (gbu_result, [_VP, _VP, _U64, _VP]),
     "gbu_utf8_to_utf16be_async": (_I32, [_VP, _VP, _U64, _VP, _U64, _VP, _VP]),
     "gbu_utf16be_to_utf8_async": (_I32, [_VP, _VP, _U64, _VP, _U64, _VP, _VP]),
     "gbu_validate_utf8": (gbu_result, [_VP, _VP, _U64, _VP]),
@@ -209,6 +214,26 @@ def gbu_utf8_length_from_utf16be(ctx, d_in, n_units, stream=0) -> Result:
 
 def gbu_validate_utf16be(ctx, d_in, n_units, stream=0) -> Result:
     return _res(load().gbu_validate_utf16be(ctx, d_in, n_units, stream))
+
+
+def gbu_utf8_to_utf32le(ctx, d_in, n_bytes, d_out, cap_units, stream=0) -> Result:
+    return _res(load().gbu_utf8_to_utf32le(ctx, d_in, n_bytes, d_out, cap_units, stream))
+
+
+def gbu_utf32le_to_utf8(ctx, d_in, n_units, d_out, cap_bytes, stream=0) -> Result:
+    return _res(load().gbu_utf32le_to_utf8(ctx, d_in, n_units, d_out, cap_bytes, stream))
+
+
+def gbu_utf32_length_from_utf8(ctx, d_in, n_bytes, stream=0) -> Result:
+    return _res(load().gbu_utf32_length_from_utf8(ctx, d_in, n_bytes, stream))
+
+
+def gbu_utf8_length_from_utf32le(ctx, d_in, n_units, stream=0) -> Result:
+    return _res(load().gbu_utf8_length_from_utf32le(ctx, d_in, n_units, stream))
+
+
+def gbu_validate_utf32le(ctx, d_in, n_units, stream=0) -> Result:
+    return _res(load().gbu_validate_utf32le(ctx, d_in, n_units, stream))
 
 
 def gbu_utf8_to_utf16be_async(ctx, d_in, n_bytes, d_out, cap_units, d_result, stream=0) -> int:

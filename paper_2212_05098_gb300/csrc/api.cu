@@ -64,6 +64,9 @@ struct gbu_ctx {
     cudaStream_t h2d = nullptr, d2h = nullptr;
     cudaEvent_t ev_in[64] = {}, ev_done[64] = {};
     gbu_result *h_slice_res = nullptr, *d_slice_res = nullptr;
+    // UTF-32 calls: per-tile counts, offsets and first errors
+    void *scratch32 = nullptr;
+    size_t scratch32_bytes = 0;
 };
 
 namespace {
@@ -236,6 +239,7 @@ void gbu_destroy(gbu_ctx *c)
     if (c->d_item_err) cudaFree(c->d_item_err);
     if (c->d_item_done) cudaFree(c->d_item_done);
     if (c->scratch) cudaFree(c->scratch);
+    if (c->scratch32) cudaFree(c->scratch32);
     if (c->io) cudaFree(c->io);
     for (int k = 0; k < 64; k++) {
         if (c->ev_in[k]) cudaEventDestroy(c->ev_in[k]);
@@ -378,6 +382,98 @@ int32_t gbu_utf8_length_from_utf16le_async(gbu_ctx *c, const uint16_t *d_in, uin
 // first slice with an encoding error ends the input (offset and valid prefix
 // shifted by the slices before it), and a total above the capacity is
 // OUTPUT_TOO_SMALL with the required length, as for the one-call form.
+// ---- UTF-32LE ------------------------------------------------------------------
+
+static bool ensure_scratch32(gbu_ctx *c, size_t bytes, cudaStream_t s)
+{
+    if (bytes <= c->scratch32_bytes) return true;
+    if (!ok(cudaStreamSynchronize(s)) || !ok(cudaDeviceSynchronize())) return false;
+    if (c->scratch32) cudaFree(c->scratch32);
+    c->scratch32 = nullptr;
+    c->scratch32_bytes = 0;
+    if (!ok(cudaMalloc(&c->scratch32, bytes))) return false;
+    c->scratch32_bytes = bytes;
+    return true;
+}
+
+static gbu_result finish32(gbu_ctx *c, cudaStream_t s)
+{
+    if (!ok(cudaStreamSynchronize(s))) return make(GBU_DEVICE_ERROR);
+    gbu_result r;
+    std::memcpy(&r, const_cast<const gbu_result *>(c->h_result), sizeof r);
+    return r;
+}
+
+static gbu_result run_utf32_in(gbu_ctx *c, const uint32_t *d_in, uint64_t n, uint8_t *d_out,
+                               uint64_t cap, bool write, void *stream)
+{
+    if (!c || (n && !d_in) || (write && cap && !d_out)) return make(GBU_INVALID_ARG);
+    if (reinterpret_cast<uintptr_t>(d_in) & 3u) return make(GBU_INVALID_ARG);
+    if (n >= kMaxUnits) return make(GBU_INVALID_ARG);
+    if (n == 0) return make(GBU_OK, 0, 0);
+    if (!ok(cudaSetDevice(c->device))) return make(GBU_DEVICE_ERROR);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const uint64_t ntiles = (n + kTile32 - 1) / kTile32;
+    if (!ensure_scratch32(c, utf32_scratch_bytes(ntiles), s)) return make(GBU_DEVICE_ERROR);
+    if (!ok(launch_utf32_to_utf8(d_in, n, d_out, write ? cap : ~0ull, write, c->scratch32,
+                                 reinterpret_cast<ResultSlot *>(c->d_result), s)))
+        return make(GBU_DEVICE_ERROR);
+    return finish32(c, s);
+}
+
+static gbu_result run_utf8_to_32(gbu_ctx *c, const uint8_t *d_in, uint64_t n, uint32_t *d_out,
+                                 uint64_t cap, bool write, void *stream)
+{
+    if (!c || (n && !d_in) || (write && cap && !d_out)) return make(GBU_INVALID_ARG);
+    if (write && (reinterpret_cast<uintptr_t>(d_out) & 3u)) return make(GBU_INVALID_ARG);
+    if (n == 0) return make(GBU_OK, 0, 0);
+    // the UTF-8 rules of Sec. 6.4, by the UTF-8 kernel (validation only)
+    const gbu_result v = run_sync(c, Op::U8toU16, d_in, n, nullptr, 0, false, stream, true);
+    if (v.status >= GBU_INVALID_ARG) return v;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const uint64_t p = v.status == GBU_OK ? n : v.in_offset;   // the valid prefix
+    const uint64_t ntiles = (p + kTile8 - 1) / kTile8;
+    if (!ensure_scratch32(c, utf32_scratch_bytes(ntiles), s)) return make(GBU_DEVICE_ERROR);
+    if (!ok(launch_utf8_to_utf32(d_in, n, p, v.status, v.in_offset, d_out, write ? cap : ~0ull,
+                                 write, c->scratch32, reinterpret_cast<ResultSlot *>(c->d_result),
+                                 s)))
+        return make(GBU_DEVICE_ERROR);
+    return finish32(c, s);
+}
+
+extern "C" {
+
+gbu_result gbu_utf32le_to_utf8(gbu_ctx *c, const uint32_t *d_in, uint64_t n, uint8_t *d_out,
+                               uint64_t cap, void *stream)
+{
+    return run_utf32_in(c, d_in, n, d_out, cap, true, stream);
+}
+
+gbu_result gbu_utf8_length_from_utf32le(gbu_ctx *c, const uint32_t *d_in, uint64_t n, void *stream)
+{
+    return run_utf32_in(c, d_in, n, nullptr, 0, false, stream);
+}
+
+gbu_result gbu_validate_utf32le(gbu_ctx *c, const uint32_t *d_in, uint64_t n, void *stream)
+{
+    gbu_result r = run_utf32_in(c, d_in, n, nullptr, 0, false, stream);
+    if (r.status < GBU_INVALID_ARG) r.out_len = 0;
+    return r;
+}
+
+gbu_result gbu_utf8_to_utf32le(gbu_ctx *c, const uint8_t *d_in, uint64_t n, uint32_t *d_out,
+                               uint64_t cap, void *stream)
+{
+    return run_utf8_to_32(c, d_in, n, d_out, cap, true, stream);
+}
+
+gbu_result gbu_utf32_length_from_utf8(gbu_ctx *c, const uint8_t *d_in, uint64_t n, void *stream)
+{
+    return run_utf8_to_32(c, d_in, n, nullptr, 0, false, stream);
+}
+
+}  // extern "C"
+
 static constexpr int kMaxSlices = 64;
 static constexpr uint64_t kMinSliceBytes = 32ull << 20;
 

@@ -14,6 +14,7 @@
 
 #include "../../include/gbutf.h"
 #include "kernels.h"
+#include "utf32.h"
 
 using namespace gbu;
 

@@ -16,7 +16,7 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
-#include "kernels.h"
+#include "utf32.h"
 
 namespace gbu {
 

@@ -95,6 +95,7 @@ bool op_big_endian(int32_t op)
 void attach_scratch(gbu_ctx *c, Job &J)
 {
     uint8_t *h = c->scratch;
+    J.chunks_done = reinterpret_cast<unsigned int *>(h + kHdrChunks);
     J.claim = reinterpret_cast<unsigned int *>(h + kHdrClaim);
     J.exit_count = reinterpret_cast<unsigned int *>(h + kHdrExit);
     J.flags = reinterpret_cast<unsigned int *>(h + kHdrFlags);
@@ -127,7 +128,7 @@ int32_t ensure_scratch(gbu_ctx *c, uint64_t chunks, cudaStream_t stream)
         c->dirty = true;
     }
     if (c->dirty) {
-        // claim = exit = flags = done = 0, first-error word = ~0, epoch = 0,
+        // chunks_done = exit = flags = done = 0, first-error word = ~0, epoch = 0,
         // and no status word may look ready
         static const uint64_t hdr[4] = {0, 0, ~0ull, 0};
         if (!ok(cudaMemcpyAsync(c->scratch, hdr, sizeof hdr, cudaMemcpyHostToDevice, stream)) ||

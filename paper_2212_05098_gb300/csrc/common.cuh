@@ -21,7 +21,12 @@ namespace gbu {
 #define GBU_THREADS 256
 #endif
 constexpr int kThreads = GBU_THREADS;         // compute threads of a CTA
-constexpr int kBlock = kThreads + 32;         // + one look-back warp
+// Look-back warps per CTA (chunk j of a CTA is looked back by warp j % kLbWarps).
+#ifndef GBU_LB_WARPS
+#define GBU_LB_WARPS 1
+#endif
+constexpr int kLbWarps = GBU_LB_WARPS;
+constexpr int kBlock = kThreads + 32 * kLbWarps + 32;   // + look-back warps and a producer warp
 constexpr unsigned kFull = 0xffffffffu;
 
 // Barrier among the kThreads compute threads only (named barrier 1), so the
@@ -42,29 +47,26 @@ __device__ __forceinline__ bool cw_sync_or(bool v)
     return r != 0;
 }
 
-// Every chunk is 8 KiB of input in both directions: 8192 UTF-8 bytes or 4096
-// UTF-16 words. Thread t always owns input bytes [32t, 32t + 32) of its chunk.
-constexpr uint32_t kChunkBytes = 32 * kThreads;   // 8192 with 256 compute threads
+// Every chunk (the unit of work of one CTA iteration, and of the look-back)
+// holds kBPT input bytes per compute thread in both directions: with 256
+// compute threads and 64 bytes each, 16 KiB = 16384 UTF-8 bytes or 8192
+// UTF-16 words. Thread t always owns input bytes [kBPT t, kBPT t + kBPT) of
+// its chunk.
+#ifndef GBU_BPT
+#define GBU_BPT 48
+#endif
+constexpr int kBPT = GBU_BPT;
+static_assert(kBPT % 16 == 0 && kBPT >= 32 && kBPT <= 64, "bytes per thread");
+constexpr uint32_t kChunkBytes = kBPT * kThreads;
 constexpr uint32_t kChunk8 = kChunkBytes;        // UTF-8 bytes per chunk
 constexpr uint32_t kChunk16 = kChunkBytes / 2;   // UTF-16 words per chunk
 // Input ring: each stage holds one chunk plus kHalo bytes on each side.
 #ifndef GBU_STAGES
-#define GBU_STAGES 2
+#define GBU_STAGES 3
 #endif
 constexpr int kStages = GBU_STAGES;
 constexpr uint32_t kHalo = 16;
 constexpr uint32_t kStageBytes = kChunkBytes + 2 * kHalo;
-// Output staging capacity per chunk. UTF-8 -> UTF-16: at most one unit per
-// input byte, plus slack. UTF-16 -> UTF-8: a chunk's valid words need at most
-// 3 * kChunk16 + 1 bytes (3 per BMP word; a high surrogate that is the chunk's
-// last word adds 4 for 1). Offsets past an error may grow further; stores and
-// the write-out are bounded by these capacities (output past an error is
-// unspecified).
-constexpr uint32_t kStage8Units = kChunk8 + 8;
-constexpr uint32_t kStage16Bytes = 3 * kChunk16 + 8;
-constexpr uint32_t kOutBufBytes =
-    (2 * kStage8Units > kStage16Bytes ? 2 * kStage8Units : kStage16Bytes) + 32;
-
 // Status codes (numerically equal to gbu_status in include/gbutf.h).
 enum : int32_t {
     kOk = 0, kHeaderBits = 1, kTooShort = 2, kTooLong = 3, kOverlong = 4,
@@ -80,24 +82,31 @@ constexpr uint64_t kFlagInclusive = 2;
 constexpr int kEpochShift = 40;
 constexpr uint32_t kEpochMask = (1u << 22) - 1;
 constexpr uint64_t kValueMask = (1ull << 40) - 1;
-// Bounded waits: a poll loop gives up after this many rounds (each round
-// sleeps ~0.1-1 us), sets the timeout flag and lets the CTA finish.
-constexpr uint32_t kSpinLimit = 1u << 21;
-
-// Back-off while polling (ns): look-back rounds that found a predecessor
-// not ready, and mbarrier waits after GBU_MBAR_SPINS plain polls.
+// Bounded waits: every wait gives up after kWaitNs nanoseconds of global
+// time (1 s by default; a build knob so that a test build can make a wait run
+// out quickly), sets the timeout flag and lets the CTA finish.
+#ifndef GBU_WAIT_NS
+#define GBU_WAIT_NS 1000000000ull
+#endif
+constexpr uint64_t kWaitNs = GBU_WAIT_NS;
+// An mbarrier wait suspends the thread in hardware until the phase completes
+// or this many nanoseconds pass, then checks the clock and waits again.
+constexpr uint32_t kSuspendNs = 20000;
+// Look-back rounds that find a predecessor not ready: the first few re-read
+// at once (an L2 round trip paces them), later ones back off (ns).
 #ifndef GBU_LB_SLEEP_SHORT
-#define GBU_LB_SLEEP_SHORT 200
+#define GBU_LB_SLEEP_SHORT 100
 #endif
 #ifndef GBU_LB_SLEEP_LONG
-#define GBU_LB_SLEEP_LONG 1000
+#define GBU_LB_SLEEP_LONG 500
 #endif
-#ifndef GBU_MBAR_SPINS
-#define GBU_MBAR_SPINS 4
-#endif
-#ifndef GBU_MBAR_SLEEP
-#define GBU_MBAR_SLEEP 500
-#endif
+
+__device__ __forceinline__ uint64_t globaltimer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 struct ResultSlot {      // layout of gbu_result
     int32_t status;
@@ -133,7 +142,8 @@ struct Job {
     uint32_t total_chunks;
     uint32_t status_capacity;       // status words in the scratch (cleared on epoch wrap)
     unsigned int *epoch;            // launch epoch: read at start, advanced by the last CTA
-    unsigned int *claim;            // next chunk to hand out
+    unsigned int *chunks_done;      // chunks processed so far (summed by the CTAs on exit)
+    unsigned int *claim;            // next chunk to hand out (when chunks are claimed)
     unsigned int *exit_count;       // CTAs that left the chunk loop
     unsigned int *flags;            // bit 0: a bounded wait timed out; bit 1: bad chunk id
     unsigned long long *status;     // [total_chunks] look-back words
@@ -177,6 +187,49 @@ __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v)
     return v;
 }
 
+// Barrier among the compute threads that also counts the threads whose `v`
+// is true (every thread gets the count).
+__device__ __forceinline__ uint32_t cw_sync_count(bool v)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.popc.u32 %0, 1, %2, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(kThreads)
+        : "memory");
+    return r;
+}
+
+// Exclusive scan of one uint32 per compute thread whose barrier also counts
+// the threads that raise `flag` (returned in *nflag). warp_tot must not be
+// written again before every thread has passed another compute-thread
+// barrier (callers alternate two arrays).
+__device__ __forceinline__ uint32_t block_exclusive_scan_flag(uint32_t v, bool flag,
+                                                              uint32_t *warp_tot, uint32_t *total,
+                                                              uint32_t *nflag)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) warp_tot[warp] = inc;
+    *nflag = cw_sync_count(flag);
+    constexpr int kWarps = kThreads / 32;
+    uint32_t t = lane < kWarps ? warp_tot[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < kWarps; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(kFull, t, o);
+        if (lane >= o) t += u;
+    }
+    *total = __shfl_sync(kFull, t, kWarps - 1);
+    const uint32_t below = __shfl_sync(kFull, t, warp > 0 ? warp - 1 : 0);
+    return (warp > 0 ? below : 0u) + inc - v;
+}
+
 // Exclusive scan of one uint32 per compute thread (kThreads threads), with
 // one barrier: every warp scans its lanes and posts its total; after the
 // barrier every thread adds up the totals of the warps before its own.
@@ -207,14 +260,52 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *w
     return (warp > 0 ? below : 0u) + inc - v;
 }
 
+// One look-back window, already loaded: w[m] is the status word of the
+// predecessor 32 m + lane places before the first one not yet summed. Sets
+// *ready when every predecessor up to the nearest inclusive prefix (or the
+// whole window) has published, *found when the window holds an inclusive
+// prefix; returns this lane's share of the sum of values up to and including
+// the nearest inclusive prefix (warp-sum it when ready).
+template <int kLook>
+__device__ __forceinline__ uint64_t lookback_window(const uint64_t (&w)[kLook], uint32_t epoch,
+                                                    bool *ready, bool *found)
+{
+    const int lane = threadIdx.x & 31;
+    bool rd = true, fd = false;
+    uint64_t part = 0;
+#pragma unroll
+    for (int m = 0; m < kLook; m++) {
+        if (fd) break;                               // warp-uniform
+        const uint64_t x = w[m];
+        const bool current = ((x >> kEpochShift) & kEpochMask) == epoch;
+        const uint64_t flag = current ? x >> 62 : 0;
+        const uint32_t inc = __ballot_sync(kFull, flag == kFlagInclusive);
+        const uint32_t nr = __ballot_sync(kFull, flag == 0);
+        // ready when no word before the nearest inclusive one is missing
+        const uint32_t upto = inc ? ((inc & (0u - inc)) - 1u) : 0xFFFFFFFFu;
+        if (nr & upto) rd = false;
+        const uint64_t v = x & kValueMask;
+        if (inc) {
+            const int l = __ffs(inc) - 1;            // nearest predecessor with a full prefix
+            if (lane <= l) part += v;
+            fd = true;
+        } else {
+            part += v;
+        }
+    }
+    *ready = rd;
+    *found = fd;
+    return part;
+}
+
 // Decoupled look-back, run by one full warp for the item chunk `k` (k > 0)
 // whose status words start at `status` (the item's first chunk). Each round
 // reads kLook words per lane (the 32 * kLook nearest predecessors
 // not yet summed) in one L2 round trip, sums aggregates back to the nearest
 // inclusive prefix, and moves on if there is none. Returns the chunk's
-// exclusive prefix (all lanes). On a wait longer than kSpinLimit polls, or as
-// soon as another CTA of the launch gave up, it sets the timeout flag and
-// returns what it has.
+// exclusive prefix (all lanes). On a wait longer than kWaitNs, or as soon as
+// another CTA of the launch gave up, it sets the timeout flag and returns what
+// it has.
 // kLook is a tuning parameter (see Tune in kernels.h).
 template <int kLook>
 __device__ __forceinline__ uint64_t lookback(const unsigned long long *status, uint32_t k,
@@ -226,6 +317,7 @@ __device__ __forceinline__ uint64_t lookback(const unsigned long long *status, u
     uint64_t excl = 0;
     int64_t base = (int64_t)k - 1;
     uint32_t rounds = 0;
+    uint64_t t0 = 0;
     while (true) {
         // one round trip for the whole window, then one pass over it from the
         // nearest predecessor backwards (only the raw words stay in registers)
@@ -264,13 +356,15 @@ __device__ __forceinline__ uint64_t lookback(const unsigned long long *status, u
             continue;
         }
         ++rounds;
-        const bool other = (rounds & 63u) == 0 &&
-                           *reinterpret_cast<volatile unsigned int *>(flags) != 0;
-        if (rounds > kSpinLimit || __any_sync(kFull, other)) {
+        if (rounds == 1) t0 = globaltimer_ns();
+        const bool other = (rounds & 15u) == 0 &&
+                           (*reinterpret_cast<volatile unsigned int *>(flags) != 0 ||
+                            globaltimer_ns() - t0 > kWaitNs);
+        if (__any_sync(kFull, other)) {
             if (lane == 0) atomicOr(flags, 1u);
             return excl;
         }
-        __nanosleep(rounds < 8 ? GBU_LB_SLEEP_SHORT : GBU_LB_SLEEP_LONG);
+        if (rounds > 3) __nanosleep(rounds < 16 ? GBU_LB_SLEEP_SHORT : GBU_LB_SLEEP_LONG);
     }
 }
 
@@ -279,9 +373,9 @@ __device__ __forceinline__ uint64_t lookback(const unsigned long long *status, u
 // the words are picked without selects.
 template <int Q>
 __device__ __forceinline__ void store_blocks(const uint4 *sv, uint8_t *d0, uint32_t nblk,
-                                             uint32_t sh)
+                                             uint32_t sh, uint32_t first, uint32_t stride)
 {
-    for (uint32_t b = threadIdx.x; b < nblk; b += kThreads) {
+    for (uint32_t b = first; b < nblk; b += stride) {
         const uint4 A = sv[b], B = sv[b + 1];                       // bytes 16b .. 16b+31
         const uint32_t x[8] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w};
         uint4 v;
@@ -312,10 +406,10 @@ __device__ __forceinline__ void block_store_bytes(const uint8_t *s_src, uint8_t 
     const uint4 *sv = reinterpret_cast<const uint4 *>(s_src);
     uint8_t *d0 = dst + head;
     switch ((head >> 2) & 3u) {
-    case 0: store_blocks<0>(sv, d0, nblk, sh); break;
-    case 1: store_blocks<1>(sv, d0, nblk, sh); break;
-    case 2: store_blocks<2>(sv, d0, nblk, sh); break;
-    default: store_blocks<3>(sv, d0, nblk, sh); break;
+    case 0: store_blocks<0>(sv, d0, nblk, sh, tid, kThreads); break;
+    case 1: store_blocks<1>(sv, d0, nblk, sh, tid, kThreads); break;
+    case 2: store_blocks<2>(sv, d0, nblk, sh, tid, kThreads); break;
+    default: store_blocks<3>(sv, d0, nblk, sh, tid, kThreads); break;
     }
     const uint32_t tail0 = head + 16u * nblk;
     if (tid < nbytes - tail0) dst[tail0 + tid] = s_src[tail0 + tid];
@@ -417,13 +511,42 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
-// Bounded wait for a phase of an mbarrier; false when the wait gave up.
+// Non-blocking test for the completion of a phase of an mbarrier.
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// try_wait with a suspend-time hint: if the phase is not complete, the thread
+// is suspended until it completes or about hint_ns nanoseconds pass.
+__device__ __forceinline__ bool mbar_try_wait_hint(uint64_t *bar, uint32_t parity, uint32_t hint_ns)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for a phase of an mbarrier; false when the wait gave up
+// (after kWaitNs of global time).
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
 {
-    for (uint32_t i = 0; i < kSpinLimit; i++) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (i > GBU_MBAR_SPINS) __nanosleep(GBU_MBAR_SLEEP);
-    }
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    do {
+        if (mbar_try_wait_hint(bar, parity, kSuspendNs)) return true;
+    } while (globaltimer_ns() - t0 < kWaitNs);
     return false;
 }
 

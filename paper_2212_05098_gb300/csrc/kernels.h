@@ -8,7 +8,7 @@
 
 // Resident CTAs per SM the kernel is compiled for (register budget).
 #ifndef GBU_MIN_BLOCKS
-#define GBU_MIN_BLOCKS 3
+#define GBU_MIN_BLOCKS 2
 #endif
 
 namespace gbu {
@@ -16,8 +16,8 @@ namespace gbu {
 constexpr int kMinBlocks = GBU_MIN_BLOCKS;
 
 // Scratch header shared by every job launch on one scratch area.
-constexpr size_t kHdrClaim = 0, kHdrExit = 4, kHdrFlags = 8, kHdrDone = 12, kHdrErr = 16,
-                 kHdrEpoch = 24;
+constexpr size_t kHdrChunks = 0, kHdrExit = 4, kHdrFlags = 8, kHdrDone = 12, kHdrErr = 16,
+                 kHdrEpoch = 24, kHdrClaim = 28;
 constexpr size_t kHdrResult = 64;   // result slot (used where no caller slot exists)
 constexpr size_t kHeaderBytes = 256;
 

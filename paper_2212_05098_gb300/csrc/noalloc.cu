@@ -98,6 +98,8 @@ extern "C" gbu_result gbu_utf8_to_utf16le_noalloc(const uint8_t *d_in, uint64_t 
         cudaMemsetAsync(base + 16, 0xFF, 8, s) != cudaSuccess)
         return fail(GBU_DEVICE_ERROR);
 
+    J.chunks_done = reinterpret_cast<unsigned int *>(base + kHdrChunks);
+
     J.claim = reinterpret_cast<unsigned int *>(base + kHdrClaim);
     J.exit_count = reinterpret_cast<unsigned int *>(base + kHdrExit);
     J.flags = reinterpret_cast<unsigned int *>(base + kHdrFlags);

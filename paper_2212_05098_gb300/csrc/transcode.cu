@@ -1,26 +1,35 @@
 // Persistent, validating UTF-8 <-> UTF-16LE transcoding kernel (paper Sec. 6
 // and Sec. 7) over a job of one or more inputs.
 //
-// Work decomposition. Every input ("item") is cut into 8 KiB chunks; the
-// chunks of all items of a job are numbered globally and handed out in order
-// by an atomic counter. A persistent grid (a few CTAs per SM) loops over them:
-//   * thread 0 claims chunks ahead and loads each one, with 16 bytes of
-//     context on either side, into a ring of kStages shared-memory stages by
-//     a 1-D TMA bulk copy completing on the stage's mbarrier;
-//   * the 256 threads classify the chunk (thread t owns bytes [32t, 32t+32)),
-//     count its output, scan the counts across the CTA and publish the
-//     chunk's aggregate for the decoupled look-back;
-//   * a ninth warp looks back for the chunk's offset as soon as its aggregate
-//     is out and publishes the inclusive prefix;
-//   * the compute threads assemble the chunk's output into one of kDepth
-//     shared-memory staging buffers and write it out with 16-byte stores
-//     kDepth iterations later, when its offset is long known.
-// The compute warps thus practically never wait on a look-back, and the TMA
-// ring loads the next chunk while the current one is processed.
+// Work decomposition. Every input ("item") is cut into chunks of kChunkBytes
+// input bytes (12 KiB: 48 bytes per compute thread); the chunks of all items
+// of a job are numbered globally and claimed in order from a counter by a
+// persistent grid (two CTAs per SM). A CTA has kThreads compute threads, a
+// producer warp and a look-back warp:
+//   * the producer (one lane) claims each chunk just ahead of its processing
+//     (once the compute warps have counted the chunk before it, so that the
+//     chunks of all CTAs are processed about in the order of their numbers)
+//     and loads it, with 16 bytes of context on either side, into a ring of
+//     kStages shared-memory stages by a 1-D TMA bulk copy completing on the
+//     stage's "full" mbarrier; a stage is refilled as soon as every compute
+//     warp has arrived on its "empty" mbarrier, after the producer has
+//     recorded the chunk's first error and counted the chunk done;
+//   * the compute threads classify a chunk (thread t owns input bytes
+//     [48t, 48t + 48)), count its output and scan the counts across the CTA;
+//     thread 0 publishes the chunk's aggregate for the decoupled look-back;
+//   * the look-back warp looks back for the chunk's offset, several chunks at
+//     a time, publishes the inclusive prefix and hands the offset back;
+//   * the compute threads assemble the chunk's output into a shared-memory
+//     staging buffer and write it out with 16-byte stores kDepth iterations
+//     later, when its offset is long known.
+// Compute warps run no look-back, TMA issue or result accounting, and meet
+// at two CTA barriers per chunk: the scan's, which also tells every thread
+// whether any wait gave up, and the one that frees the staging buffer after
+// the write-out.
 //
 // Ownership: a UTF-8 unit belongs to the thread holding its end position
-// (see chunk8 below); a UTF-16 surrogate pair belongs to the owner of its
-// high surrogate. Errors are located by the exact local rules described with
+// (see the UTF-8 section below); a UTF-16 surrogate pair is split between
+// its two words. Errors are located by the exact local rules described with
 // each chunk body; the minimum (position, kind) over a chunk and then over
 // the item is the sequential decoder's first error (the paper's ell).
 #include "kernels.h"
@@ -30,6 +39,27 @@ namespace gbu {
 namespace {
 
 constexpr uint32_t kB7 = 0x80808080u;
+constexpr int kW = kBPT / 4;     // 32-bit words a compute thread owns per chunk
+constexpr int kU16 = kBPT / 2;   // UTF-16 words a compute thread owns per chunk
+static_assert(kW % 4 == 0, "16-byte loads");
+// Output staging per chunk: at most 2 bytes per UTF-8 input byte, 3 per
+// UTF-16 input word, plus slack for the 16-byte block reads of the
+// write-out.
+constexpr uint32_t kOutBytes = 2 * kChunk8 > 3 * kChunk16 ? 2 * kChunk8 : 3 * kChunk16;
+constexpr uint32_t kOutBuf = kOutBytes + 48;
+constexpr uint32_t kWarpOutBytes = kOutBytes;   // bound of a thread's staging (one buffer)
+
+// Positions i in [0, kBPT) (bytes or UTF-16 words counted by `unit`) with
+// lo <= vt + i < hi, as a bit mask.
+__device__ __forceinline__ uint64_t pos_mask(int64_t vt, int64_t lo, int64_t hi, int n)
+{
+    int64_t a = lo - vt, b = hi - vt;
+    if (a < 0) a = 0;
+    if (b > n) b = n;
+    if (b <= a) return 0;
+    const uint64_t upto = b >= 64 ? ~0ull : ((1ull << b) - 1ull);
+    return upto & ~((1ull << a) - 1ull);
+}
 
 // ===========================================================================
 // UTF-8 -> UTF-16LE chunk (paper Sec. 6)
@@ -101,20 +131,70 @@ __device__ __forceinline__ uint32_t spread4(uint32_t m4)
     return ((m4 * 0x00204081u) & 0x01010101u) << 7;
 }
 
+// The thread's words from the stage: w[0] = bytes -4..-1, w[1..kW] its own
+// bytes, w[kW+1] = bytes kBPT..kBPT+3. Outside an interior chunk, bytes
+// outside the input read as zero; *vmask gets the owned positions inside the
+// input, *outside / *masked whether none / not all of them are.
+struct Edge {
+    uint64_t vmask;
+    bool outside, masked, straddle;
+};
+
+__device__ __forceinline__ void load_words(uint32_t (&w)[kW + 2], const uint8_t *stage)
+{
+    const uint8_t *sp = stage + kHalo + kBPT * threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < kW / 4; q++) {
+        const uint4 a = reinterpret_cast<const uint4 *>(sp)[q];
+        w[1 + 4 * q] = a.x;
+        w[2 + 4 * q] = a.y;
+        w[3 + 4 * q] = a.z;
+        w[4 + 4 * q] = a.w;
+    }
+    w[0] = *reinterpret_cast<const uint32_t *>(sp - 4);
+    w[kW + 1] = *reinterpret_cast<const uint32_t *>(sp + kBPT);
+}
+
+__device__ __forceinline__ void load8(uint32_t (&w)[kW + 2], const uint8_t *stage, bool interior,
+                                      int64_t vt, int64_t lo, int64_t hi, Edge &e)
+{
+    load_words(w, stage);
+    e.vmask = ~0ull;
+    e.outside = e.masked = e.straddle = false;
+    if (interior) return;
+    e.outside = vt + kBPT <= lo || vt >= hi;
+    if (e.outside) {
+#pragma unroll
+        for (int j = 0; j < kW + 2; j++) w[j] = 0;
+        e.vmask = 0;
+        e.masked = true;
+        return;
+    }
+    if (vt < lo || vt + kBPT > hi) {   // straddles an end of the input
+        e.masked = e.straddle = true;
+        e.vmask = pos_mask(vt, lo, hi, kBPT);
+#pragma unroll
+        for (int j = 0; j < kW; j++) w[1 + j] = mask_word_bytes(w[1 + j], vt + 4 * j, lo, hi);
+    }
+    if (vt - 4 < lo || vt + kBPT + 4 > hi) {
+        w[0] = mask_word_bytes(w[0], vt - 4, lo, hi);
+        w[kW + 1] = mask_word_bytes(w[kW + 1], vt + kBPT, lo, hi);
+    }
+}
+
 // Exact local rule for every owned position of a flagged thread (rare path).
-// Re-reads the thread's bytes (positions -4 .. 35) from the stage and
-// recomputes the end positions, so the hot path keeps its words in
-// registers. Returns the key of the first error, or ~0.
+// Re-reads the thread's bytes (positions -4 .. kBPT+3) from the stage and
+// recomputes the end positions. Returns the key of the first error, or ~0.
 __device__ __noinline__ uint64_t first_error_exact8(const uint8_t *stage, int64_t vt, int64_t lo,
                                                     int64_t hi, uint32_t t_off)
 {
-    const uint8_t *sp = stage + kHalo + 32 * threadIdx.x;
-    uint32_t w[10];
-    for (int j = 0; j < 10; j++)
+    const uint8_t *sp = stage + kHalo + kBPT * threadIdx.x;
+    uint32_t w[kW + 2];
+    for (int j = 0; j < kW + 2; j++)
         w[j] = mask_word_bytes(*reinterpret_cast<const uint32_t *>(sp - 4 + 4 * j), vt - 4 + 4 * j,
                                lo, hi);
     uint32_t units = 0;
-    for (int i = 0; i < 32; i++) {
+    for (int i = 0; i < kBPT; i++) {
         const int j = (i >> 2) + 1;
         const int sh = (i & 3) * 8;
         const uint32_t xf = __funnelshift_r(w[j], w[j + 1], sh);   // bytes i .. i+3
@@ -164,199 +244,240 @@ __device__ __noinline__ uint64_t first_error_exact8(const uint8_t *stage, int64_
     return ~0ull;
 }
 
+// Phase 2 reuses phase 1's end positions (kept in registers) or recomputes
+// them from the words.
+#ifndef GBU_CARRY_ENDS
+#define GBU_CARRY_ENDS 1
+#endif
+constexpr bool kCarryEnds = GBU_CARRY_ENDS != 0;
+
 struct St8 {
-    uint32_t w[10];    // w[0]: bytes -4..-1, w[1..8]: own bytes 0..31, w[9]: 32..35
-    uint32_t end[8];   // end-position indicators (bit 7 of each byte)
-    uint32_t vmask;    // owned positions inside the input
+    uint32_t end[kCarryEnds ? kW : 1];   // end-position indicators (bit 7 of each byte)
     uint32_t bad;      // the fast check fired
     bool skip;         // the whole warp lies outside the input (warp-uniform)
-    bool warp3, warp4;
+    bool warp3, warp4; // the warp holds >= E0 / >= F0 leads (warp-uniform)
 };
 
-// Structure check (expected continuations = continuations), C0/C1 check
-// and end positions of one thread (Sec. 6.1, 6.4); returns its unit count.
-// k3: the warp holds >= E0 leads (else every >= E0 / >= F0 term is zero and
-// dropped). ORs its >= F0 leads into any4.
-template <bool k3>
-__device__ __forceinline__ uint32_t structure8(St8 &st, const uint32_t *w, bool wmasked,
-                                               uint32_t &bad, uint32_t &any4)
+// One pass over the thread's words: classification, the exact structure
+// check, the C0/C1 check, the value checks of 3- and 4-byte leads, and the
+// end positions (Sec. 6.1, 6.4); returns the thread's unit count. k3 / k4:
+// the warp holds >= E0 / >= F0 leads (else their terms are zero and dropped).
+template <bool k3, bool k4>
+__device__ __forceinline__ uint32_t structure8(const uint32_t (&w)[kW + 2], uint32_t (&end)[kW],
+                                               bool wmasked, uint64_t vmask, uint32_t &bad)
 {
-    Cls cl[10];
+    Cls cp = classify(w[0]);
+    if (!k3) cp.c3 = 0;
+    if (!k4) cp.c4 = 0;
+    uint32_t ec_prev = 0, c4_pp = 0, cnt = 0;
 #pragma unroll
-    for (int j = 0; j < 10; j++) {
-        cl[j] = classify(w[j]);
-        if (!k3) cl[j].c3 = cl[j].c4 = 0;
-    }
-    // leads in the look-behind word shape the units at the first positions
-    any4 = cl[0].c4;
-    uint32_t ec[9], cnt = 0;
-#pragma unroll
-    for (int j = 1; j <= 8; j++) {
-        const uint32_t exp = back(cl[j - 1].c2, cl[j].c2, 8) | back(cl[j - 1].c3, cl[j].c3, 16) |
-                             back(cl[j - 1].c4, cl[j].c4, 24);
-        bad |= exp ^ cl[j].ct;
-        ec[j - 1] = exp & cl[j].ct;
-        // C0 / C1: 2-byte leads whose bits 4..1 are zero
-        bad |= cl[j].c2 & ~cl[j].c3 & zero_bytes(w[j] & 0x1E1E1E1Eu);
-        any4 |= cl[j].c4;
-    }
-    // continuations the last leads expect at positions 32..34
-    const uint32_t exp9 = (cl[8].c2 >> 24) | (cl[8].c3 >> 16) | (cl[8].c4 >> 8);
-    bad |= exp9 & ~cl[9].ct;
-    ec[8] = exp9 & cl[9].ct;
-    if (!wmasked) {
-#pragma unroll
-        for (int j = 1; j <= 8; j++) {
-            const uint32_t e = (~ahead(ec[j - 1], ec[j], 8) | back(cl[j - 1].c4, cl[j].c4, 16)) & kB7;
-            st.end[j - 1] = e;
+    for (int j = 1; j <= kW + 1; j++) {
+        const uint32_t x = w[j];
+        Cls c = classify(x);
+        if (!k3) c.c3 = 0;
+        if (!k4) c.c4 = 0;
+        uint32_t exp;
+        if (j <= kW) {
+            exp = back(cp.c2, c.c2, 8);
+            if (k3) exp |= back(cp.c3, c.c3, 16);
+            if (k4) exp |= back(cp.c4, c.c4, 24);
+            bad |= exp ^ c.ct;
+            // C0 / C1: leads >= C0 whose low 7 bits are below 0x42 (no carry
+            // crosses a byte: 0x7F + 0x3E < 0x100)
+            const uint32_t x7 = x & 0x7F7F7F7Fu;
+            bad |= c.c2 & ~(x7 + 0x3E3E3E3Eu);
+            if (k3 || k4) {
+                const uint32_t y = ahead(x, w[j + 1], 8);   // the next byte of each position
+                if (k3) {
+                    // E0 + 80..9F (overlong), ED + A0..BF (surrogate): a byte
+                    // that is E0 when bit 5 of the next byte is clear, or ED
+                    // when it is set
+                    const uint32_t y5 = y << 2;
+                    const uint32_t m = ((y5 >> 7) & 0x01010101u) * 0x0Du;
+                    bad |= zero_bytes(x ^ 0xE0E0E0E0u ^ m);
+                }
+                if (k4) {
+                    // F0 + 80..8F (overlong), F4 + 90..BF (too large): a byte
+                    // that is F0 when bits 5 and 4 of the next byte are clear,
+                    // or F4 when one is set; and F5..FF (the low 7 bits reach
+                    // 0x80 when 0x0B is added)
+                    const uint32_t y54 = (y << 2) | (y << 3);
+                    const uint32_t m = (y54 >> 5) & 0x04040404u;
+                    bad |= zero_bytes(x ^ 0xF0F0F0F0u ^ m);
+                    bad |= (x7 + 0x0B0B0B0Bu) & x & kB7;
+                }
+            }
+        } else {
+            // continuations the last leads expect at positions kBPT.. kBPT+2
+            exp = cp.c2 >> 24;
+            if (k3) exp |= cp.c3 >> 16;
+            if (k4) exp |= cp.c4 >> 8;
+            bad |= exp & ~c.ct;
+        }
+        const uint32_t ec = exp & c.ct;
+        if (j >= 2) {   // the end positions of word j-1
+            uint32_t e = ~ahead(ec_prev, ec, 8);
+            if (k4) e |= back(c4_pp, cp.c4, 16);
+            e &= kB7;
+            if (wmasked) e &= spread4((uint32_t)(vmask >> (4 * (j - 2))) & 0xFu);
+            end[j - 2] = e;
             cnt += __popc(e);
         }
-    } else {
-#pragma unroll
-        for (int j = 1; j <= 8; j++) {
-            uint32_t e = (~ahead(ec[j - 1], ec[j], 8) | back(cl[j - 1].c4, cl[j].c4, 16)) & kB7;
-            e &= spread4((st.vmask >> (4 * (j - 1))) & 0xFu);
-            st.end[j - 1] = e;
-            cnt += __popc(e);
-        }
+        c4_pp = cp.c4;
+        ec_prev = ec;
+        cp = c;
     }
     return cnt;
 }
 
-// Load, classify, check structure, count units. Returns the thread's count.
-__device__ __forceinline__ uint32_t chunk8_phase1(St8 &st, const uint8_t *stage, int64_t vt,
-                                                  int64_t lo, int64_t hi)
+// Load, classify, check, count units. Returns the thread's count.
+__device__ __forceinline__ uint32_t chunk8_phase1(St8 &st, const uint8_t *stage, bool interior,
+                                                  int64_t vt, int64_t lo, int64_t hi)
 {
-    const uint8_t *sp = stage + kHalo + 32 * threadIdx.x;
-    const uint4 a = *reinterpret_cast<const uint4 *>(sp);
-    const uint4 b = *reinterpret_cast<const uint4 *>(sp + 16);
-    uint32_t *w = st.w;
-    w[1] = a.x; w[2] = a.y; w[3] = a.z; w[4] = a.w;
-    w[5] = b.x; w[6] = b.y; w[7] = b.z; w[8] = b.w;
-    w[0] = *reinterpret_cast<const uint32_t *>(sp - 4);
-    w[9] = *reinterpret_cast<const uint32_t *>(sp + 32);
+    uint32_t w[kW + 2];
+    Edge e;
+    load8(w, stage, interior, vt, lo, hi, e);
     st.bad = 0;
-    st.vmask = 0xFFFFFFFFu;
-    bool masked = false;
-    // A chunk whose bytes and context all lie inside the input (the common
-    // case; the test is the same for every thread) needs none of the edge
-    // handling below.
-    const int64_t v0 = vt - 32 * (int64_t)threadIdx.x;
-    const bool interior = v0 - 4 >= lo && v0 + (int64_t)kChunk8 + 4 <= hi;
+    st.skip = false;
     if (!interior) {
-        // threads wholly outside the input (the tail of an item's last chunk)
-        // count nothing; a warp wholly outside skips the chunk body
-        const bool outside = vt + 32 <= lo || vt >= hi;
-        st.skip = __all_sync(kFull, outside);
+        // a warp wholly outside the input (the tail of an item's last chunk)
+        // skips the chunk body
+        st.skip = __all_sync(kFull, e.outside);
         if (st.skip) {
-            st.vmask = 0;
             st.warp3 = st.warp4 = false;
+#pragma unroll
+            for (int j = 0; j < (kCarryEnds ? kW : 1); j++) st.end[j] = 0;
             return 0;
         }
-        if (outside) {
-#pragma unroll
-            for (int j = 0; j < 10; j++) w[j] = 0;
-            st.vmask = 0;
-            masked = true;
-        } else if (vt < lo || vt + 32 > hi) {   // straddles an end of the input
-            masked = true;
-            st.vmask = 0;
-#pragma unroll
-            for (int i = 0; i < 32; i++)
-                if (vt + i >= lo && vt + i < hi) st.vmask |= 1u << i;
-#pragma unroll
-            for (int j = 0; j < 8; j++) w[1 + j] = mask_word_bytes(w[1 + j], vt + 4 * j, lo, hi);
-        }
-        if (!outside && (vt - 4 < lo || vt + 36 > hi)) {
-            w[0] = mask_word_bytes(w[0], vt - 4, lo, hi);
-            w[9] = mask_word_bytes(w[9], vt + 32, lo, hi);
-        }
-    } else {
-        st.skip = false;
     }
     // some thread of the warp masks its end positions (warp-uniform, so the
     // unmasked warps branch around that work instead of predicating it)
-    const bool wmasked = !interior && __any_sync(kFull, masked);
-
-    // leads >= E0 (3/4-byte) anywhere in the warp, the look-behind word
-    // included: without them the phase below drops their terms
-    uint32_t any3 = 0;
+    const bool wmasked = !interior && __any_sync(kFull, e.masked);
+    // leads >= E0 (3/4-byte) and >= F0 anywhere in the warp, the look-behind
+    // word included: without them the pass below drops their terms
+    uint32_t a3 = 0, a4 = 0;
 #pragma unroll
-    for (int j = 0; j < 9; j++) any3 |= w[j] & (w[j] << 1) & (w[j] << 2);
-    st.warp3 = __any_sync(kFull, (any3 & kB7) != 0);
-    uint32_t bad = 0, any4 = 0, cnt;
-    if (st.warp3) {
-        cnt = structure8<true>(st, w, wmasked, bad, any4);
-        st.warp4 = __any_sync(kFull, any4 != 0);
-    } else {
-        cnt = structure8<false>(st, w, wmasked, bad, any4);
-        st.warp4 = false;
+    for (int j = 0; j <= kW; j++) {
+        const uint32_t x3 = w[j] & (w[j] << 1) & (w[j] << 2);
+        a3 |= x3;
+        a4 |= x3 & (w[j] << 3);
     }
-    if (st.warp3) {
-        // E0 + 80..9F (overlong), ED + A0..BF (surrogate): a byte that is E0
-        // when bit 5 of the next byte is clear, or ED when it is set
-#pragma unroll
-        for (int j = 1; j <= 8; j++) {
-            const uint32_t y5 = ahead(w[j], w[j + 1], 8) << 2;   // bit 5 of the next byte, at bit 7
-            const uint32_t m = ((y5 >> 7) & 0x01010101u) * 0x0Du;  // 0x0D where it is set
-            bad |= zero_bytes(w[j] ^ 0xE0E0E0E0u ^ m);
-        }
-    }
-    if (st.warp4) {
-        // F0 + 80..8F (overlong), F4 + 90..BF (too large): a byte that is F0
-        // when bits 5 and 4 of the next byte are clear, or F4 when one is
-        // set; and F5..FF (the low 7 bits reach 0x80 when 0x0B is added)
-#pragma unroll
-        for (int j = 1; j <= 8; j++) {
-            const uint32_t y = ahead(w[j], w[j + 1], 8);
-            const uint32_t y54 = (y << 2) | (y << 3);              // bit 7: bit 5 or 4 of the next byte
-            const uint32_t m = (y54 >> 5) & 0x04040404u;           // 0x04 where set
-            bad |= zero_bytes(w[j] ^ 0xF0F0F0F0u ^ m);
-            bad |= ((w[j] & 0x7F7F7F7Fu) + 0x0B0B0B0Bu) & w[j] & 0x80808080u;
-        }
-    }
+    st.warp3 = __any_sync(kFull, (a3 & kB7) != 0);
+    st.warp4 = __any_sync(kFull, (a4 & kB7) != 0);
+    uint32_t bad = 0, cnt, end[kW];
+    if (st.warp4)
+        cnt = structure8<true, true>(w, end, wmasked, e.vmask, bad);
+    else if (st.warp3)
+        cnt = structure8<true, false>(w, end, wmasked, e.vmask, bad);
+    else
+        cnt = structure8<false, false>(w, end, wmasked, e.vmask, bad);
     st.bad = bad;
+    if (kCarryEnds) {
+#pragma unroll
+        for (int j = 0; j < kW; j++) st.end[kCarryEnds ? j : 0] = end[j];
+    }
     return cnt;
 }
 
-// Exact first error (flagged threads) and staging of the units.
-// Units at the end positions (Eq. W_sum, W_out), four positions at a time
-// on two registers of 16-bit lanes, stored at p in order. k3 / k4: the warp
+// End positions of a thread whose words passed the fast check (phase 2
+// recomputes them word by word instead of keeping them in registers across
+// chunks): every continuation byte of its words is then expected, so a
+// position ends a unit when the next byte is not a continuation or when it is
+// the third byte of a 4-byte sequence; the byte after its last position
+// counts as a continuation only where the thread's last leads expect it (a
+// stray continuation there is the next thread's error, and the valid prefix
+// ends before it). Called for words j = 1 .. kW in order.
+template <bool k3, bool k4>
+struct EndsValid {
+    const uint32_t (&w)[kW + 2];
+    const bool wmasked;
+    const uint64_t vmask;
+    uint32_t ct, c4_prev;
+    static __device__ __forceinline__ uint32_t cont(uint32_t x) { return x & ~(x << 1) & kB7; }
+    static __device__ __forceinline__ uint32_t ge_f0(uint32_t x)
+    {
+        return x & (x << 1) & (x << 2) & (x << 3) & kB7;
+    }
+    __device__ __forceinline__ EndsValid(const uint32_t (&w_)[kW + 2], bool wm, uint64_t vm)
+        : w(w_), wmasked(wm), vmask(vm)
+    {
+        c4_prev = k4 ? ge_f0(w[0]) : 0u;
+        ct = cont(w[1]);
+    }
+    __device__ __forceinline__ uint32_t operator()(int j)
+    {
+        const uint32_t x = w[j];
+        uint32_t ct_next;
+        if (j < kW) {
+            ct_next = cont(w[j + 1]);
+        } else {
+            const uint32_t c2 = x & (x << 1) & kB7;
+            uint32_t exp = c2 >> 24;
+            if (k3) {
+                const uint32_t c3 = c2 & (x << 2);
+                exp |= c3 >> 16;
+                if (k4) exp |= (c3 & (x << 3)) >> 8;
+            }
+            ct_next = exp & cont(w[kW + 1]);
+        }
+        const uint32_t c4 = k4 ? ge_f0(x) : 0u;
+        uint32_t e = ~ahead(ct, ct_next, 8);
+        if (k4) e |= back(c4_prev, c4, 16);
+        e &= kB7;
+        if (wmasked) e &= spread4((uint32_t)(vmask >> (4 * (j - 1))) & 0xFu);
+        ct = ct_next;
+        c4_prev = c4;
+        return e;
+    }
+};
+
+// End positions from an array (the exact ones of structure8).
+struct EndsArray {
+    const uint32_t (&end)[kW];
+    __device__ __forceinline__ uint32_t operator()(int j) const { return end[j - 1]; }
+};
+
+// Units at the end positions (Eq. W_sum, W_out), four positions at a time on
+// two registers of 16-bit lanes, stored at p in order. k3 / k4: the warp
 // holds 3- or 4-byte leads (4-byte leads are also >= E0, so k4 implies k3).
-template <bool k3, bool k4, bool kBE>
-__device__ __forceinline__ void assemble8(const St8 &st, uint16_t *p)
+template <bool k3, bool k4, bool kBE, typename EndFn>
+__device__ __forceinline__ void assemble8(const uint32_t (&w)[kW + 2], EndFn end_of, uint16_t *p)
 {
-    const uint32_t *w = st.w;
-    uint32_t s[9], c3[9], c4[9];
-#pragma unroll
-    for (int j = 0; j < 9; j++) {
-        // >= E0 / >= F0 at bit 7 of each byte (the other bits are not
-        // used: the masks below replicate bit 7)
-        if (k3) c3[j] = w[j] & (w[j] << 1) & (w[j] << 2);
-        if (k4) c4[j] = c3[j] & (w[j] << 3);
-        const uint32_t na = prmt(w[j], 0, 0xBA98);        // 0xFF where byte >= 0x80
-        s[j] = w[j] & ~(na & 0xC0C0C0C0u);                // tag bits stripped
+    uint32_t s_prev, c3_prev = 0, c4_prev = 0;
+    {
+        const uint32_t x = w[0];
+        const uint32_t na = prmt(x, 0, 0xBA98);
+        s_prev = x & ~(na & 0xC0C0C0C0u);
+        // >= E0 / >= F0 at bit 7 of each byte (the other bits are not used:
+        // the masks below replicate bit 7)
+        if (k3) c3_prev = x & (x << 1) & (x << 2);
+        if (k4) c4_prev = c3_prev & (x << 3);
     }
 #pragma unroll
-    for (int j = 1; j <= 8; j++) {
-        const uint32_t na = prmt(w[j], 0, 0xBA98);
-        const uint32_t s1 = back(s[j - 1], s[j], 8) & na;          // W_-1 where end byte is not ASCII
-        uint32_t wa = prmt(s[j], 0, 0x4140) + (prmt(s1, 0, 0x4140) << 6);
-        uint32_t wb = prmt(s[j], 0, 0x4342) + (prmt(s1, 0, 0x4342) << 6);
+    for (int j = 1; j <= kW; j++) {
+        const uint32_t x = w[j];
+        const uint32_t na = prmt(x, 0, 0xBA98);            // 0xFF where byte >= 0x80
+        const uint32_t s = x & ~(na & 0xC0C0C0C0u);         // tag bits stripped
+        uint32_t c3 = 0, c4 = 0;
+        if (k3) c3 = x & (x << 1) & (x << 2);
+        if (k4) c4 = c3 & (x << 3);
+        const uint32_t s1 = back(s_prev, s, 8) & na;        // W_-1 where the end byte is not ASCII
+        uint32_t wa = prmt(s, 0, 0x4140) + (prmt(s1, 0, 0x4140) << 6);
+        uint32_t wb = prmt(s, 0, 0x4342) + (prmt(s1, 0, 0x4342) << 6);
         if (k3) {
             // W_-2 (low 4 bits) where the byte two back is a 3/4-byte lead
-            const uint32_t m3 = prmt(c3[j - 1], c3[j], 0xDCBA);
-            const uint32_t s2 = back(s[j - 1], s[j], 16) & m3 & 0x0F0F0F0Fu;
+            const uint32_t m3 = prmt(c3_prev, c3, 0xDCBA);
+            const uint32_t s2 = back(s_prev, s, 16) & m3 & 0x0F0F0F0Fu;
             wa += prmt(s2, 0, 0x4140) << 12;
             wb += prmt(s2, 0, 0x4342) << 12;
         }
         if (k4) {
             // surrogates: high at the third byte of a 4-byte sequence,
             // low at its fourth byte (Eq. W_out)
-            const uint32_t hma = prmt(c4[j - 1], c4[j], 0xBBAA);
-            const uint32_t hmb = prmt(c4[j - 1], c4[j], 0xDDCC);
-            const uint32_t lma = prmt(c4[j - 1], c4[j], 0xAA99);
-            const uint32_t lmb = prmt(c4[j - 1], c4[j], 0xCCBB);
+            const uint32_t hma = prmt(c4_prev, c4, 0xBBAA);
+            const uint32_t hmb = prmt(c4_prev, c4, 0xDDCC);
+            const uint32_t lma = prmt(c4_prev, c4, 0xAA99);
+            const uint32_t lmb = prmt(c4_prev, c4, 0xCCBB);
             const uint32_t ha = ((wa >> 4) & 0x0FFF0FFFu) + 0xD7C0D7C0u;
             const uint32_t hb = ((wb >> 4) & 0x0FFF0FFFu) + 0xD7C0D7C0u;
             wa = ((ha & hma) | (wa & ~hma)) | (lma & 0xDC00DC00u);
@@ -366,36 +487,76 @@ __device__ __forceinline__ void assemble8(const St8 &st, uint16_t *p)
             wa = prmt(wa, 0, 0x2301);
             wb = prmt(wb, 0, 0x2301);
         }
-        const uint32_t e = st.end[j - 1];
+        const uint32_t e = end_of(j);
         if (e & 0x00000080u) *p++ = (uint16_t)wa;
         if (e & 0x00008000u) *p++ = (uint16_t)(wa >> 16);
         if (e & 0x00800000u) *p++ = (uint16_t)wb;
         if (e & 0x80000000u) *p++ = (uint16_t)(wb >> 16);
+        s_prev = s;
+        c3_prev = c3;
+        c4_prev = c4;
     }
 }
 
+// A thread the fast check flagged (rare; kept out of line so that it costs
+// the common path no registers): the exact first error, and the units of the
+// valid prefix at their exact end positions (a stray continuation ends the
+// valid prefix before it).
 template <bool kWrite, bool kBE>
-__device__ __forceinline__ void chunk8_phase2(St8 &st, const uint8_t *stage, uint8_t *obuf,
-                                              uint32_t t_off, int64_t vt, int64_t lo, int64_t hi,
-                                              unsigned long long *s_err)
+__device__ __noinline__ void exact8(const uint8_t *stage, bool interior, int64_t vt, int64_t lo,
+                                    int64_t hi, uint32_t t_off, bool wmasked, uint16_t *p,
+                                    unsigned long long *s_err)
+{
+    const uint64_t key = first_error_exact8(stage, vt, lo, hi, t_off);
+    if (key != ~0ull) atomicMin(s_err, key);
+    if (!kWrite) return;
+    uint32_t w[kW + 2], end[kW], b = 0;
+    Edge e;
+    load8(w, stage, interior, vt, lo, hi, e);
+    structure8<true, true>(w, end, wmasked, e.vmask, b);
+    assemble8<true, true, kBE>(w, EndsArray{end}, p);
+}
+
+// Phase 2 of a thread: exact first error (flagged threads) and staging of the
+// units at p. t_off: the thread's output offset in the chunk (for the error
+// key).
+template <bool kWrite, bool kBE>
+__device__ __forceinline__ void chunk8_phase2(const St8 &st, const uint8_t *stage, bool interior,
+                                              uint16_t *p, uint32_t t_off, int64_t vt, int64_t lo,
+                                              int64_t hi, unsigned long long *s_err)
 {
     if (st.skip) return;
-    // Threads straddling an end of the input see the bytes outside it as
-    // zeros (ASCII), which neither create nor hide an error inside it, so
-    // the fast check covers them as well.
-    if (st.bad) {
-        const uint64_t key = first_error_exact8(stage, vt, lo, hi, t_off);
-        if (key != ~0ull) atomicMin(s_err, key);
+    if (!kWrite) {
+        // Threads straddling an end of the input see the bytes outside it
+        // as zeros (ASCII), which neither create nor hide an error inside
+        // it, so the fast check covers them as well.
+        if (st.bad) exact8<false, kBE>(stage, interior, vt, lo, hi, t_off, false, p, s_err);
+        return;
     }
-    if (!kWrite) return;
+    uint32_t w[kW + 2];
+    Edge e;
+    load8(w, stage, interior, vt, lo, hi, e);
+    const bool wmasked = !interior && __any_sync(kFull, e.masked);
+    if (st.bad) {
+        exact8<true, kBE>(stage, interior, vt, lo, hi, t_off, wmasked, p, s_err);
+        return;
+    }
     // the 3/4-byte parts only in warps that hold such leads (warp-uniform)
-    uint16_t *p = reinterpret_cast<uint16_t *>(obuf) + t_off;
-    if (st.warp4)
-        assemble8<true, true, kBE>(st, p);
-    else if (st.warp3)
-        assemble8<true, false, kBE>(st, p);
-    else
-        assemble8<false, false, kBE>(st, p);
+    if (kCarryEnds) {
+        const uint32_t(&end)[kW] = reinterpret_cast<const uint32_t(&)[kW]>(st.end);
+        if (st.warp4)
+            assemble8<true, true, kBE>(w, EndsArray{end}, p);
+        else if (st.warp3)
+            assemble8<true, false, kBE>(w, EndsArray{end}, p);
+        else
+            assemble8<false, false, kBE>(w, EndsArray{end}, p);
+    } else if (st.warp4) {
+        assemble8<true, true, kBE>(w, EndsValid<true, true>(w, wmasked, e.vmask), p);
+    } else if (st.warp3) {
+        assemble8<true, false, kBE>(w, EndsValid<true, false>(w, wmasked, e.vmask), p);
+    } else {
+        assemble8<false, false, kBE>(w, EndsValid<false, false>(w, wmasked, e.vmask), p);
+    }
 }
 
 // ===========================================================================
@@ -436,7 +597,7 @@ __device__ __forceinline__ uint32_t surr_lanes(uint32_t w)    // D800-DFFF (exac
     return (v - 0x00010001u) & ~v & 0x80008000u;
 }
 
-__device__ __forceinline__ uint32_t lane16(const uint32_t *w, int i)   // word i, i in [-2, 18)
+__device__ __forceinline__ uint32_t lane16(const uint32_t *w, int i)   // word i, i in [-2, kU16 + 2)
 {
     return (w[(i + 2) >> 1] >> (16 * ((i + 2) & 1))) & 0xFFFFu;
 }
@@ -454,8 +615,7 @@ __device__ __forceinline__ uint32_t enc3(uint32_t u)
 }
 
 struct St16 {
-    uint32_t w[10];    // w[0]: words -2,-1; w[1..8]: own words 0..15; w[9]: words 16,17
-    uint32_t vmask;
+    uint32_t vmask;    // owned words inside the input
     bool slow;         // the thread straddles an end of the input
     bool skip;         // the whole warp lies outside the input (warp-uniform)
     bool sur, only12;  // the warp holds surrogates / only words below U+0800 (warp-uniform)
@@ -466,79 +626,81 @@ __device__ __forceinline__ uint32_t unit_keep(int64_t u, int64_t lo, int64_t hi)
     return (u >= lo && u < hi) ? 0xFFFFu : 0u;
 }
 
+// The thread's words (two UTF-16 words each) from the stage, as for load8:
+// w[0] = words -2, -1; w[1..kW] its own; w[kW+1] = words kU16, kU16+1.
+// Words outside the input read as zero; UTF-16BE words are byte-swapped.
 template <bool kBE>
-__device__ __forceinline__ uint32_t chunk16_phase1(St16 &st, const uint8_t *stage, int64_t vt,
-                                                   int64_t lo, int64_t hi)
+__device__ __forceinline__ void load16(uint32_t (&w)[kW + 2], const uint8_t *stage, bool interior,
+                                       int64_t vt, int64_t lo, int64_t hi, Edge &e)
 {
-    const uint8_t *sp = stage + kHalo + 32 * threadIdx.x;
-    const uint4 a = *reinterpret_cast<const uint4 *>(sp);
-    const uint4 b = *reinterpret_cast<const uint4 *>(sp + 16);
-    uint32_t *w = st.w;
-    w[1] = a.x; w[2] = a.y; w[3] = a.z; w[4] = a.w;
-    w[5] = b.x; w[6] = b.y; w[7] = b.z; w[8] = b.w;
-    w[0] = *reinterpret_cast<const uint32_t *>(sp - 4);
-    w[9] = *reinterpret_cast<const uint32_t *>(sp + 32);
-    st.vmask = 0xFFFFu;
-    bool edge = false, masked = false;
-    // A chunk whose words and context all lie inside the input (the common
-    // case; the same test for every thread) needs none of the edge handling.
-    const int64_t v0 = vt - 16 * (int64_t)threadIdx.x;
-    const bool interior = v0 - 2 >= lo && v0 + (int64_t)kChunk16 + 2 <= hi;
+    load_words(w, stage);
+    e.vmask = kU16 >= 32 ? 0xFFFFFFFFull : ((1ull << kU16) - 1ull);
+    e.outside = e.masked = e.straddle = false;
+    if (!interior) {
+        e.outside = vt + kU16 <= lo || vt >= hi;
+        if (e.outside) {
+#pragma unroll
+            for (int j = 0; j < kW + 2; j++) w[j] = 0;
+            e.vmask = 0;
+            e.masked = true;
+        } else {
+            if (vt < lo || vt + kU16 > hi) {   // straddles an end of the input
+                e.straddle = e.masked = true;
+                e.vmask = pos_mask(vt, lo, hi, kU16);
+#pragma unroll
+                for (int j = 0; j < kW; j++)
+                    w[1 + j] &= unit_keep(vt + 2 * j, lo, hi) | (unit_keep(vt + 2 * j + 1, lo, hi) << 16);
+            }
+            if (vt - 2 < lo || vt + kU16 + 2 > hi) {
+                w[0] &= unit_keep(vt - 2, lo, hi) | (unit_keep(vt - 1, lo, hi) << 16);
+                w[kW + 1] &= unit_keep(vt + kU16, lo, hi) | (unit_keep(vt + kU16 + 1, lo, hi) << 16);
+            }
+        }
+    }
+    if (kBE) {   // UTF-16BE: swap the bytes of every word once, then as UTF-16LE
+#pragma unroll
+        for (int j = 0; j < kW + 2; j++) w[j] = prmt(w[j], 0, 0x2301);
+    }
+}
+
+template <bool kBE>
+__device__ __forceinline__ uint32_t chunk16_phase1(St16 &st, const uint8_t *stage, bool interior,
+                                                   int64_t vt, int64_t lo, int64_t hi)
+{
+    uint32_t w[kW + 2];
+    Edge e;
+    load16<kBE>(w, stage, interior, vt, lo, hi, e);
+    st.vmask = (uint32_t)e.vmask;
+    st.skip = false;
+    st.slow = e.straddle;
     if (!interior) {
         // threads wholly outside the input count nothing; a warp wholly
         // outside skips the chunk body
-        const bool outside = vt + 16 <= lo || vt >= hi;
-        st.skip = __all_sync(kFull, outside);
+        st.skip = __all_sync(kFull, e.outside);
         if (st.skip) {
-            st.vmask = 0;
             st.slow = st.sur = st.only12 = false;
             return 0;
         }
-        if (outside) {
-#pragma unroll
-            for (int j = 0; j < 10; j++) w[j] = 0;
-            st.vmask = 0;
-            masked = true;
-        } else if (vt < lo || vt + 16 > hi) {   // straddles an end of the input
-            edge = masked = true;
-            st.vmask = 0;
-#pragma unroll
-            for (int i = 0; i < 16; i++)
-                if (vt + i >= lo && vt + i < hi) st.vmask |= 1u << i;
-#pragma unroll
-            for (int j = 0; j < 8; j++)
-                w[1 + j] &= unit_keep(vt + 2 * j, lo, hi) | (unit_keep(vt + 2 * j + 1, lo, hi) << 16);
-        }
-        if (!outside && (vt - 2 < lo || vt + 18 > hi)) {
-            w[0] &= unit_keep(vt - 2, lo, hi) | (unit_keep(vt - 1, lo, hi) << 16);
-            w[9] &= unit_keep(vt + 16, lo, hi) | (unit_keep(vt + 17, lo, hi) << 16);
-        }
-    } else {
-        st.skip = false;
     }
     // some thread of the warp counts only part of its words (warp-uniform)
-    const bool wmasked = !interior && __any_sync(kFull, masked);
-    if (kBE) {   // UTF-16BE: swap the bytes of every word once, then as UTF-16LE
-#pragma unroll
-        for (int j = 0; j < 10; j++) w[j] = prmt(w[j], 0, 0x2301);
-    }
+    const bool wmasked = !interior && __any_sync(kFull, e.masked);
     // does the warp hold words of U+0800 and above? (warp-uniform; words
     // outside the input are zero)
     uint32_t top5 = 0;
 #pragma unroll
-    for (int j = 0; j < 8; j++) top5 |= w[1 + j] & 0xF800F800u;
+    for (int j = 0; j < kW; j++) top5 |= w[1 + j] & 0xF800F800u;
     st.only12 = !__any_sync(kFull, top5 != 0);
     // per word: 1 + [>=80] + [>=800] - [surrogate]: 1-3 bytes, 2 for either
     // half of a pair
     uint32_t cnt = 0, anysur = 0;
     if (!wmasked && st.only12) {
-        cnt = 16;
+        cnt = kU16;
 #pragma unroll
-        for (int j = 0; j < 8; j++) cnt += __popc(ge80_lanes(w[1 + j]));
+        for (int j = 0; j < kW; j++) cnt += __popc(ge80_lanes(w[1 + j]));
     } else if (!wmasked) {
-        cnt = 16;
+        cnt = kU16;
 #pragma unroll
-        for (int j = 0; j < 8; j++) {
+        for (int j = 0; j < kW; j++) {
             const uint32_t x = w[1 + j];
             const uint32_t ga = ge80_lanes(x), gb = ge800_lanes(x), s = surr_lanes(x);
             cnt += __popc(ga) + __popc(gb) - __popc(s);
@@ -546,7 +708,7 @@ __device__ __forceinline__ uint32_t chunk16_phase1(St16 &st, const uint8_t *stag
         }
     } else {
 #pragma unroll
-        for (int j = 0; j < 8; j++) {
+        for (int j = 0; j < kW; j++) {
             const uint32_t x = w[1 + j];
             const uint32_t ga = ge80_lanes(x), gb = ge800_lanes(x), s = surr_lanes(x);
             const uint32_t vm = (((st.vmask >> (2 * j)) & 1u) << 15) | (((st.vmask >> (2 * j + 1)) & 1u) << 31);
@@ -555,25 +717,24 @@ __device__ __forceinline__ uint32_t chunk16_phase1(St16 &st, const uint8_t *stag
         }
     }
     st.sur = __any_sync(kFull, anysur != 0);
-    st.slow = edge;
     return cnt;
 }
 
-// UTF-8 bytes of 16 units, two units at a time on 16-bit lanes
-// (Fig. 1(a)): lead F (the unit itself, C0 | u >> 6, or E0 | u >> 12),
+// UTF-8 bytes of the thread's words, two at a time on 16-bit lanes
+// (Fig. 1(a)): lead F (the word itself, C0 | u >> 6, or E0 | u >> 12),
 // second byte S (80 | u & 3F, or 80 | (u >> 6) & 3F in the 3-byte form) and
-// third byte T (80 | u & 3F); each unit stores its 1-3 bytes at p.
+// third byte T (80 | u & 3F); each word stores its 1-3 bytes at p.
 // A surrogate pair's 4 bytes (Sec. 7.3) are split between its halves, 2
 // each: with U = (high & 3FF) + 40 (the code point >> 10), the high
 // surrogate stores F0 | U >> 8 and 80 | (U >> 2) & 3F, the low one
 // 80 | (high & 3) << 4 | (low >> 6) & F and 80 | low & 3F.
-// kSur: the units may hold surrogates (validly paired; the pair may cross
+// kSur: the words may hold surrogates (validly paired; the pair may cross
 // into the next thread, the low half then stores its 2 bytes there).
 template <bool kSur>
-__device__ __forceinline__ void encode_bmp(const uint32_t *w, uint8_t *p)
+__device__ __forceinline__ void encode_bmp(const uint32_t (&w)[kW + 2], uint8_t *p)
 {
 #pragma unroll
-    for (int j = 1; j <= 8; j++) {
+    for (int j = 1; j <= kW; j++) {
         const uint32_t x = w[j];
         const uint32_t m2 = prmt(ge80_lanes(x), 0, 0xBB99);     // 0xFFFF on lanes >= 0x80
         uint32_t m3 = prmt(ge800_lanes(x), 0, 0xBB99);          // 0xFFFF on lanes >= 0x800
@@ -589,7 +750,7 @@ __device__ __forceinline__ void encode_bmp(const uint32_t *w, uint8_t *p)
             const uint32_t hu = (x & 0x03FF03FFu) + 0x00400040u;  // U of a high surrogate
             const uint32_t fh = ((hu >> 8) & 0x00070007u) | 0x00F000F0u;
             const uint32_t sh = ((hu >> 2) & 0x003F003Fu) | 0x00800080u;
-            const uint32_t prev = __funnelshift_l(w[j - 1], x, 16);   // the unit before each lane
+            const uint32_t prev = __funnelshift_l(w[j - 1], x, 16);   // the word before each lane
             const uint32_t fl = ((prev & 0x00030003u) << 4) | (x6 & 0x000F000Fu) | 0x00800080u;
             f = (((fl & ml) | (fh & ~ml)) & ms) | (f & ~ms);
             s = (((t & ml) | (sh & ~ml)) & ms) | (s & ~ms);
@@ -606,12 +767,23 @@ __device__ __forceinline__ void encode_bmp(const uint32_t *w, uint8_t *p)
     }
 }
 
-template <bool kWrite>
-__device__ __forceinline__ void chunk16_phase2(const St16 &st, uint8_t *obuf, uint32_t t_off,
-                                               int64_t vt, int64_t lo, unsigned long long *s_err)
+// Validation and staging of the thread's bytes at obuf (output offset t_off
+// in the chunk; obuf holds the chunk's bytes from offset wb). The warp-uniform
+// flags come from phase 1; the per-thread ones are recomputed from the input
+// edges.
+template <bool kWrite, bool kBE>
+__device__ __forceinline__ void chunk16_phase2(St16 st, const uint8_t *stage, bool interior,
+                                               uint8_t *obuf, uint32_t t_off, uint32_t wb, int64_t vt,
+                                               int64_t lo, int64_t hi, unsigned long long *s_err)
 {
-    if (st.skip || st.vmask == 0) return;   // nothing of the input here
-    const uint32_t *w = st.w;
+    if (st.skip) return;
+    uint32_t w[kW + 2];
+    Edge e;
+    load16<kBE>(w, stage, interior, vt, lo, hi, e);
+    st.vmask = (uint32_t)e.vmask;
+    st.slow = e.straddle;
+    if (st.vmask == 0) return;   // nothing of the input here
+    if (!kWrite && !st.sur && !st.slow) return;   // valid and nothing to write
     bool slow = st.slow;
     if (st.sur && !slow) {
         // sequencing (Sec. 7.4): a word is a low surrogate exactly when the
@@ -622,23 +794,23 @@ __device__ __forceinline__ void chunk16_phase2(const St16 &st, uint8_t *obuf, ui
         auto lo_lanes = [](uint32_t x) { return surr_lanes(x) & (x << 5); };
         uint32_t v = 0, h_prev = hi_lanes(w[0]);
 #pragma unroll
-        for (int j = 1; j <= 8; j++) {
+        for (int j = 1; j <= kW; j++) {
             const uint32_t h = hi_lanes(w[j]);
             v |= __funnelshift_l(h_prev, h, 16) ^ lo_lanes(w[j]);
             h_prev = h;
         }
-        v |= (h_prev ^ (lo_lanes(w[9]) << 16)) & 0x80000000u;
+        v |= (h_prev ^ (lo_lanes(w[kW + 1]) << 16)) & 0x80000000u;
         slow = v != 0;
     }
     if (!slow) {
         // every word of this thread is valid
         if (!kWrite) return;
-        uint8_t *p = obuf + t_off;
+        uint8_t *p = obuf + (t_off - wb);
         if (st.sur) {
             encode_bmp<true>(w, p);
         } else if (st.only12) {
 #pragma unroll
-            for (int i = 0; i < 16; i++) {
+            for (int i = 0; i < kU16; i++) {
                 const uint32_t u = lane16(w, i);
                 const bool big = u >= 0x80u;
                 const uint32_t v = big ? enc2(u) : u;
@@ -654,7 +826,7 @@ __device__ __forceinline__ void chunk16_phase2(const St16 &st, uint8_t *obuf, ui
     uint64_t key = ~0ull;
     uint32_t o = t_off;
 #pragma unroll
-    for (int i = 0; i < 16; i++) {
+    for (int i = 0; i < kU16; i++) {
         const uint32_t u = lane16(w, i), pv = lane16(w, i - 1), nx = lane16(w, i + 1);
         const bool is_hi = (u & 0xFC00u) == 0xD800u;
         const bool is_lo = (u & 0xFC00u) == 0xDC00u;
@@ -673,8 +845,8 @@ __device__ __forceinline__ void chunk16_phase2(const St16 &st, uint8_t *obuf, ui
             v = c3 ? enc3(u) : (c2 ? enc2(u) : u);
         }
         if ((st.vmask >> i) & 1u) {
-            if (kWrite && o + len <= kStage16Bytes) {
-                uint8_t *q = obuf + o;
+            if (kWrite && o - wb + len <= kWarpOutBytes) {
+                uint8_t *q = obuf + (o - wb);
                 q[0] = (uint8_t)v;
                 if (len >= 2) q[1] = (uint8_t)(v >> 8);
                 if (len >= 3) q[2] = (uint8_t)(v >> 16);
@@ -691,32 +863,50 @@ __device__ __forceinline__ void chunk16_phase2(const St16 &st, uint8_t *obuf, ui
 // ===========================================================================
 
 struct Ring {
-    uint64_t full[kStages];        // mbarrier per stage (TMA completion)
+    uint64_t full[kStages];        // mbarrier per stage: TMA completion (producer)
+    uint64_t empty[kStages];       // mbarrier per stage: every compute warp is done with it
     Item item[kStages];
-    uint32_t chunk[kStages], itidx[kStages], end[kStages];
+    uint32_t chunk[kStages], end[kStages];
 };
 
-// Thread 0: start the TMA load of chunk c (claimed earlier) into `slot`; `it`
-// is its item index and, in a batch, *pre its descriptor, both fetched
-// earlier (the descriptor by cp.async, waited for here).
-// Returns false (and marks the slot as the end) when the job is exhausted.
-__device__ __forceinline__ bool produce(const Job &J, uint32_t c, uint32_t it, const Item *pre,
-                                        int slot, uint8_t *stages, Ring &R)
+// What the warps know of one chunk of this CTA (slot: the chunk's number in
+// the CTA's sequence, modulo kSlots), from its load to its accounting.
+struct ChunkRec {
+    uint64_t excl;               // look-back warp: output units of the item before the chunk
+    unsigned long long err;      // compute threads (phase 2): first-error key, ~0 if none
+    uint8_t *out;                // producer: the item's output, capacity, operation
+    uint64_t cap;
+    uint32_t op;
+    uint32_t chunk, chunk_base, nchunks, itidx;   // producer
+    uint32_t agg;                // compute thread 0: the chunk's output units
+    uint32_t end;                // producer / compute thread 0: no chunk here
+};
+
+// Producer lane: load global chunk c into stage `slot` and describe it in
+// `rec` (descriptor and item index fetched here). Returns false (and marks
+// the stage and the record as the end) when the job is exhausted.
+__device__ __forceinline__ bool produce(const Job &J, uint32_t c, int slot, uint8_t *stages,
+                                        Ring &R, ChunkRec &rec)
 {
+    rec.err = ~0ull;
     if (c >= J.total_chunks) {
+        rec.end = 1;
         R.end[slot] = 1;
         mbar_arrive(&R.full[slot]);
         return false;
     }
-    if (J.items) {
-        cp_async_wait_all();
-        R.item[slot] = *pre;
-    } else {
-        R.item[slot] = J.item0;
-    }
-    const Item I = R.item[slot];
+    const uint32_t it = J.chunk_item ? J.chunk_item[c] : 0u;
+    const Item I = J.items ? J.items[it] : J.item0;
+    rec.out = I.out;
+    rec.cap = I.cap;
+    rec.op = I.op;
+    rec.chunk = c;
+    rec.chunk_base = I.chunk_base;
+    rec.nchunks = I.nchunks;
+    rec.itidx = it;
+    rec.end = 0;
+    R.item[slot] = I;
     R.chunk[slot] = c;
-    R.itidx[slot] = it;
     R.end[slot] = 0;
     const int64_t ub = (I.op & kOpUtf16) ? 2 : 1;
     const int64_t v0b = (int64_t)(c - I.chunk_base) * kChunkBytes;   // virtual byte offset
@@ -736,32 +926,25 @@ __device__ __forceinline__ bool produce(const Job &J, uint32_t c, uint32_t it, c
     return true;
 }
 
-struct Pending {                 // a processed chunk waiting for its offset
-    Item item;
-    uint32_t chunk, itidx, agg, end;
-};
-
-struct Done {                    // what the look-back warp keeps of a chunk until it is written
-    uint64_t excl;
-    uint32_t chunk, itidx, nchunks, agg;
-};
-
-// The last CTA out checks that every chunk id was handed out exactly once,
-// advances the epoch and resets the job's counters for the next launch.
-__device__ __forceinline__ void exit_job(const Job &J, uint32_t epoch)
+// Every CTA adds the chunks it processed to the job's chunk counter; the last
+// CTA out checks that they add up to the job's chunks (a counter left dirty by
+// an aborted launch shows here), advances the epoch and resets the job's
+// counters for the next launch.
+__device__ __forceinline__ void exit_job(const Job &J, uint32_t epoch, uint32_t processed)
 {
+    atomicAdd(J.chunks_done, processed);
     __threadfence();
     if (atomicAdd(J.exit_count, 1u) != gridDim.x - 1) return;
     __threadfence();   // every other CTA's accounting is visible
     if (!J.items) finalize_item(J, 0, J.item0);
-    const unsigned int claims = atomicExch(J.claim, 0u);
+    const unsigned int chunks = atomicExch(J.chunks_done, 0u);
+    *J.claim = 0;
     const unsigned int flags = atomicAdd(J.flags, 0u);
-    if (claims != J.total_chunks + gridDim.x || flags != 0) {
+    if (chunks != J.total_chunks || flags != 0) {
         // counters were left dirty by an aborted launch, or a wait gave up
         // (chunks may have been skipped, items left unfinished): no item was
         // finished reliably
-        const int32_t st = claims != J.total_chunks + gridDim.x || (flags & 2u) ? kDeviceError
-                                                                               : kDeviceTimeout;
+        const int32_t st = (flags & 1u) ? kDeviceTimeout : kDeviceError;
         for (uint32_t it = 0; it < J.num_items; it++) {
             const Item &X = J.items ? J.items[it] : J.item0;
             volatile ResultSlot *r = X.result;
@@ -780,28 +963,31 @@ __device__ __forceinline__ void exit_job(const Job &J, uint32_t epoch)
     __threadfence_system();
 }
 
-// Warps 0-7 (compute): at iteration i, wait for chunk i's stage, classify and
-// count it, scan, publish its aggregate and hand it to the look-back warp
-// (pend_bar). Then write out chunk i-kDepth from staging buffer i % kDepth
-// (its offset was computed meanwhile) and signal it (written_bar), and
-// assemble chunk i's output into the same buffer. Thread 0 also feeds the TMA
-// ring, claiming chunk ids one iteration ahead so that the claim's latency is
-// hidden. Warp 8 (look-back): for every handed-over chunk, as soon as its
-// aggregate is out, look back, publish the inclusive prefix and hand the
-// offset back (excl_bar); once the chunk is written, record its first error
-// and count it done, finishing its item's result when it is the item's last
-// chunk (a one-item job is finished by its last CTA). None of the global
-// atomics and fences of this bookkeeping sit on the compute path.
-// Output staging depth: a chunk staged in iteration i is written out in
-// iteration i + kDepth, so its offset has kDepth iterations to arrive.
-#ifndef GBU_OUT_DEPTH
-#define GBU_OUT_DEPTH 3
+// A chunk staged in iteration i is written out in iteration i + kDepth, so
+// its offset has kDepth iterations to arrive; kDepth staging buffers.
+#ifndef GBU_DEPTH
+#define GBU_DEPTH 2
 #endif
-constexpr int kDepth = GBU_OUT_DEPTH;
-// Hand-over slots (chunk j uses j % kSlots): more than the kDepth + 1
-// chunks between a hand-over and the write-out that retires it.
-constexpr int kSlots = 8;
-static_assert(kSlots > kDepth + 1, "hand-over slots");
+constexpr int kDepth = GBU_DEPTH;
+static_assert(kStages >= 2, "stages: one in use, at least one loading");
+// Chunk records (chunk j of the CTA uses slot j % kSlots): live from the
+// chunk's load (kStages chunks ahead of its phase 1) to its accounting.
+constexpr int kSlots = 16;
+static_assert(kSlots >= kStages + kDepth + kLbWarps + 2, "chunk records");
+
+// How chunks are dealt to CTAs: 0 round-robin (CTA b takes chunks b, b +
+// grid, ...); 1 claimed from a counter when a stage frees; 2 claimed from a
+// counter once the CTA's previous chunk is counted.
+#ifndef GBU_CLAIM
+#define GBU_CLAIM 2
+#endif
+constexpr int kClaim = GBU_CLAIM;
+
+// Look-backs a look-back warp runs at once.
+#ifndef GBU_LB_SLOTS
+#define GBU_LB_SLOTS 2
+#endif
+constexpr int kLbSlots = GBU_LB_SLOTS;
 
 template <bool kWrite, int kLook, bool kAnyBE>
 __global__ void __launch_bounds__(kBlock, kMinBlocks)
@@ -809,246 +995,335 @@ transcode_kernel(const Job J)
 {
     extern __shared__ __align__(128) uint8_t dyn_smem[];
     uint8_t *const stages = dyn_smem;
-    uint8_t *const obufs = dyn_smem + kStages * kStageBytes;
+    uint8_t *const obufs = dyn_smem + kStages * kStageBytes;   // kDepth output staging buffers
     __shared__ __align__(16) Ring R;
-    __shared__ __align__(16) Item s_next_item;
-    __shared__ __align__(8) uint64_t pend_bar[kSlots], excl_bar[kSlots], written_bar[kSlots];
-    __shared__ Pending s_pend[kSlots];
-    __shared__ unsigned long long s_excl[kSlots], s_errsnap[kSlots], s_err[kDepth];
-    __shared__ uint32_t s_warp[kThreads / 32 + 1];
+    __shared__ __align__(8) uint64_t pend_bar[kSlots], excl_bar[kSlots], lb_exit;
+    __shared__ ChunkRec s_rec[kSlots];
+    __shared__ uint32_t s_warp[2][kThreads / 32 + 1];
     __shared__ uint32_t s_epoch;
 
-    const uint32_t tid = threadIdx.x;
+    const uint32_t tid = threadIdx.x, lane = tid & 31;
     if (tid == 0) {
-        for (int s = 0; s < kStages; s++) mbar_init(&R.full[s], 1);
+        for (int s = 0; s < kStages; s++) {
+            mbar_init(&R.full[s], 1);
+            mbar_init(&R.empty[s], kThreads / 32);
+        }
         for (int s = 0; s < kSlots; s++) {
             mbar_init(&pend_bar[s], 1);
             mbar_init(&excl_bar[s], 1);
-            mbar_init(&written_bar[s], 1);
         }
-        for (int s = 0; s < kDepth; s++) s_err[s] = ~0ull;
+        mbar_init(&lb_exit, kLbWarps);
         fence_mbar_init();
         s_epoch = *reinterpret_cast<volatile unsigned int *>(J.epoch);
     }
     __syncthreads();
     const uint32_t epoch = s_epoch;
 
-    if (tid >= kThreads) {
-        // ---- look-back warp -------------------------------------------------
-        const bool lead = tid == kThreads;
-        bool failed = false;
-        Done dq[kDepth] = {};   // dq[m]: chunk j-1-m
-        // chunk j was written: merge its first error, count it done
-        auto account = [&](const Done &d, uint32_t j) -> bool {
-            if (!mbar_wait(&written_bar[j % kSlots], (j / kSlots) & 1u)) return false;
-            if (lead) {
-                const uint64_t key = s_errsnap[j % kSlots];
-                if (!J.items) {
-                    // one item: its result is finished by the last CTA out
-                    if (key != ~0ull) {
-                        J.err_prefix[d.chunk] = d.excl + (key & 0x7FFFu);
-                        atomicMin(&J.item_err[0], ((key >> 23) << 8) | ((key >> 15) & 0xFFu));
-                    }
-                } else if (d.nchunks == 1) {
-                    finalize_single(J, J.items ? J.items[d.itidx] : J.item0, d.agg, key);
-                } else {
-                    if (key != ~0ull) {
-                        J.err_prefix[d.chunk] = d.excl + (key & 0x7FFFu);
-                        atomicMin(&J.item_err[d.itidx], ((key >> 23) << 8) | ((key >> 15) & 0xFFu));
-                    }
-                    if (atomic_add_acq_rel(&J.item_done[d.itidx], 1u) == d.nchunks - 1)
-                        finalize_item(J, d.itidx, J.items ? J.items[d.itidx] : J.item0);
-                }
-            }
-            return true;
+    if (tid >= kThreads + 32 * kLbWarps) {
+        // ---- producer warp (lane 0): refill the ring, account for chunks ----
+        if (tid != kThreads + 32 * kLbWarps) return;
+        bool producing = true, ok = true;
+        // the next chunk of this CTA: round-robin (CTA b takes chunks b,
+        // b + grid, ...) or claimed from the job's counter
+        auto next_chunk = [&](uint32_t n) -> uint32_t {
+            if (kClaim == 0) return blockIdx.x + n * gridDim.x;
+            return atomicAdd(J.claim, 1u);
         };
+        uint32_t np = 0;   // chunks produced (the end marker included)
+        for (int s = 0; s < kStages && producing; s++, np++)
+            producing = produce(J, next_chunk(np), s, stages, R, s_rec[np % kSlots]);
+        if (!producing)   // the other look-back warps stop at the next records
+            for (int m = 1; m < kLbWarps; m++) s_rec[(np - 1 + m) % kSlots].end = 1;
+        // chunk j's first error and offset are known once its stage is
+        // released: record them, count the chunk done, finish its item's
+        // result when it is the item's last chunk (a one-item job is finished
+        // by its last CTA); then refill the stage
         uint32_t j = 0;
-        for (;; j++) {
-            const int q = j % kSlots;
-            if (!mbar_wait(&pend_bar[q], (j / kSlots) & 1u)) {
-                failed = true;
+        for (; producing || j + 1 < np; j++) {
+            if (!mbar_wait(&R.empty[j % kStages], (j / kStages) & 1u) ||
+                !mbar_wait(&excl_bar[j % kSlots], (j / kSlots) & 1u)) {
+                ok = false;
                 break;
             }
-            const Pending &P = s_pend[q];
-            if (P.end) break;
-            const uint32_t k = P.chunk - P.item.chunk_base;
-            uint64_t excl = 0;
-            if (k > 0 && !J.validate) {   // validation needs no offsets
-                excl = lookback<kLook>(J.status + P.item.chunk_base, k, epoch, J.flags);
-                if (lead)
-                    st_relaxed(&J.status[P.chunk], pack_status(kFlagInclusive, epoch, excl + P.agg));
+            const ChunkRec &r = s_rec[j % kSlots];
+            const uint64_t key = *reinterpret_cast<const volatile unsigned long long *>(&r.err);
+            if (!J.items) {
+                if (key != ~0ull) {
+                    J.err_prefix[r.chunk] = r.excl + (key & 0x7FFFu);
+                    atomicMin(&J.item_err[0], ((key >> 23) << 8) | ((key >> 15) & 0xFFu));
+                }
+            } else if (r.nchunks == 1) {
+                finalize_single(J, J.items[r.itidx], r.agg, key);
+            } else {
+                if (key != ~0ull) {
+                    J.err_prefix[r.chunk] = r.excl + (key & 0x7FFFu);
+                    atomicMin(&J.item_err[r.itidx], ((key >> 23) << 8) | ((key >> 15) & 0xFFu));
+                }
+                if (atomic_add_acq_rel(&J.item_done[r.itidx], 1u) == r.nchunks - 1)
+                    finalize_item(J, r.itidx, J.items[r.itidx]);
             }
-            Done d0;
-            d0.excl = excl;
-            d0.chunk = P.chunk;
-            d0.itidx = P.itidx;
-            d0.nchunks = P.item.nchunks;
-            d0.agg = P.agg;
+            if (producing) {
+                // kClaim 2: claim the chunk only once its predecessor in the
+                // CTA's sequence is counted, so that chunks are claimed just
+                // ahead of their processing
+                if (kClaim == 2 && !mbar_wait(&pend_bar[(np - 1) % kSlots], ((np - 1) / kSlots) & 1u)) {
+                    ok = false;
+                    break;
+                }
+                producing = produce(J, next_chunk(np), (int)(j % kStages), stages, R, s_rec[np % kSlots]);
+                np++;
+                if (!producing)
+                    for (int m = 1; m < kLbWarps; m++) s_rec[(np - 1 + m) % kSlots].end = 1;
+            }
+        }
+        if (!ok) atomicOr(J.flags, 1u);
+        // the look-back warps are done (every inclusive prefix is out)
+        if (!mbar_wait(&lb_exit, 0)) atomicOr(J.flags, 1u);
+        exit_job(J, epoch, j);
+        return;
+    }
+    if (tid >= kThreads) {
+        // ---- look-back warps: warp p handles this CTA's chunks j = p (mod kLbWarps)
+        // Once chunk j is counted (and its aggregate published): the
+        // look-back, the inclusive prefix published and the offset handed
+        // back. Up to kLbSlots look-backs run at once: every
+        // round loads the windows of all of them before checking any, so that
+        // one L2 round trip serves them all, and a chunk whose predecessors
+        // have not all published yet does not hold up the chunks after it.
+        constexpr int kSl = kLook * kLbSlots <= 8 ? kLbSlots : (8 / kLook > 0 ? 8 / kLook : 1);
+        const uint32_t p = (tid - kThreads) >> 5;
+        const bool lead = lane == 0;
+        const uint64_t start_word = pack_status(kFlagInclusive, epoch, 0);
+        bool failed = false, ending = false;
+        uint32_t next = p, live = 0;
+        uint32_t s_j[kSl], s_chunk[kSl], s_base0[kSl], s_agg[kSl];
+        int64_t s_pos[kSl];    // next predecessor to read (index in the item)
+        uint64_t s_acc[kSl];   // sum of the predecessors read so far
+#pragma unroll
+        for (int m = 0; m < kSl; m++) {
+            s_j[m] = s_chunk[m] = s_base0[m] = s_agg[m] = 0;
+            s_pos[m] = 0;
+            s_acc[m] = 0;
+        }
+        uint64_t t_idle = 0;
+        uint32_t idle_rounds = 0;
+        auto finish = [&](uint32_t j, uint64_t excl) {
             __syncwarp();
             if (lead) {
-                s_excl[q] = excl;
-                mbar_arrive(&excl_bar[q]);
+                s_rec[j % kSlots].excl = excl;
+                mbar_arrive(&excl_bar[j % kSlots]);
             }
-            if (j >= kDepth && !account(dq[kDepth - 1], j - kDepth)) {
-                failed = true;
-                break;
-            }
+        };
+        while (true) {
+            // admit the chunks counted since the last round (waiting only
+            // when nothing else is in flight)
+            while (!ending && __popc(live) < kSl) {
+                const int q = next % kSlots;
+                const uint32_t par = (next / kSlots) & 1u;
+                const bool ready = live == 0 ? __all_sync(kFull, mbar_wait(&pend_bar[q], par))
+                                             : __all_sync(kFull, mbar_test(&pend_bar[q], par));
+                if (!ready) {
+                    if (live == 0) failed = true;
+                    break;
+                }
+                const ChunkRec &r = s_rec[q];
+                if (r.end) {
+                    ending = true;
+                    break;
+                }
+                const uint32_t agg = r.agg;
+                const uint32_t k = r.chunk - r.chunk_base;
+                if (k == 0 || J.validate) {   // validation needs no offsets
+                    finish(next, 0);
+                } else {
+                    const int m = __ffs(~live) - 1;
 #pragma unroll
-            for (int m = kDepth - 1; m > 0; m--) dq[m] = dq[m - 1];
-            dq[0] = d0;
+                    for (int mm = 0; mm < kSl; mm++)
+                        if (mm == m) {
+                            s_j[mm] = next;
+                            s_chunk[mm] = r.chunk;
+                            s_base0[mm] = r.chunk_base;
+                            s_agg[mm] = agg;
+                            s_pos[mm] = (int64_t)k - 1;
+                            s_acc[mm] = 0;
+                        }
+                    live |= 1u << m;
+                }
+                next += kLbWarps;
+            }
+            if (failed || (live == 0 && ending)) break;
+            if (live == 0) continue;
+            // one round for every look-back in flight: all loads, then checks
+            uint64_t w[kSl][kLook];
+#pragma unroll
+            for (int m = 0; m < kSl; m++) {
+                if (!((live >> m) & 1u)) continue;
+#pragma unroll
+                for (int i = 0; i < kLook; i++) {
+                    const int64_t idx = s_pos[m] - 32 * i - (int64_t)lane;
+                    w[m][i] = idx >= 0 ? ld_relaxed(&J.status[s_base0[m] + idx]) : start_word;
+                }
+            }
+            bool progress = false;
+#pragma unroll
+            for (int m = 0; m < kSl; m++) {
+                if (!((live >> m) & 1u)) continue;
+                bool ready, found;
+                const uint64_t part = lookback_window<kLook>(w[m], epoch, &ready, &found);
+                if (!ready) continue;
+                progress = true;
+                s_acc[m] += warp_sum_u64(part);
+                if (found) {
+                    if (lead)
+                        st_relaxed(&J.status[s_chunk[m]],
+                                   pack_status(kFlagInclusive, epoch, s_acc[m] + s_agg[m]));
+                    finish(s_j[m], s_acc[m]);
+                    live &= ~(1u << m);
+                } else {
+                    s_pos[m] -= 32 * kLook;
+                }
+            }
+            if (progress) {
+                t_idle = 0;
+                idle_rounds = 0;
+            } else {
+                // back off while predecessors are late (the first rounds
+                // re-read at once: an L2 round trip paces them)
+                if (++idle_rounds > 2) __nanosleep(idle_rounds < 16 ? GBU_LB_SLEEP_SHORT : GBU_LB_SLEEP_LONG);
+                // predecessors not ready: give up after kWaitNs without
+                // progress, or as soon as another CTA of the launch gave up
+                const uint64_t now = globaltimer_ns();
+                if (t_idle == 0) t_idle = now;
+                const bool stop = now - t_idle > kWaitNs ||
+                                  *reinterpret_cast<volatile unsigned int *>(J.flags) != 0;
+                if (__any_sync(kFull, stop)) {
+                    failed = true;
+                    break;
+                }
+            }
         }
-        // the compute warps stop after writing out their last kDepth chunks
-#pragma unroll
-        for (int m = kDepth; m > 0; m--)
-            if (!failed && j >= (uint32_t)m && !account(dq[m - 1], j - m)) failed = true;
         if (lead) {
             if (failed) atomicOr(J.flags, 1u);
-            exit_job(J, epoch);
+            mbar_arrive(&lb_exit);
         }
         return;
     }
 
     // ---- compute warps ------------------------------------------------------
-    // write out chunk j (staging buffer j&1) once its offset is known; false
-    // if the wait for the offset gave up
-    auto write_out = [&](uint32_t j) -> bool {
-        const int q = j % kSlots;
-        if (!mbar_wait(&excl_bar[q], (j / kSlots) & 1u)) return false;
-        if (kWrite) {
-            const Pending &P = s_pend[q];
-            const uint64_t excl = s_excl[q];
-            const bool u16 = (P.item.op & kOpUtf16) != 0;
+    // write out chunk jd (staging buffer jd % kDepth) once its offset is known;
+    // false if the wait for the offset gave up
+    auto write_out = [&](uint32_t jd) -> bool {
+        const int q = jd % kSlots;
+        if (!mbar_wait(&excl_bar[q], (jd / kSlots) & 1u)) return false;
+        const ChunkRec &r = s_rec[q];
+        const uint64_t excl = r.excl;
+        if (excl < r.cap) {
+            const bool u16 = (r.op & kOpUtf16) != 0;
             const uint32_t ub = u16 ? 1u : 2u;                       // output unit bytes
-            const uint32_t stage_units = u16 ? kStage16Bytes : kStage8Units;
-            if (excl < P.item.cap) {
-                const uint64_t room = P.item.cap - excl;
-                uint32_t nw = P.agg < stage_units ? P.agg : stage_units;
-                if (nw > room) nw = (uint32_t)room;
-                block_store_bytes(obufs + (size_t)(j % kDepth) * kOutBufBytes, P.item.out + excl * ub,
-                                  nw * ub);
-            }
-        }
-        if (tid == 0) {
-            s_errsnap[q] = s_err[j % kDepth];
-            s_err[j % kDepth] = ~0ull;
-            mbar_arrive(&written_bar[q]);
+            uint64_t nw = r.agg;
+            if (nw > r.cap - excl) nw = r.cap - excl;
+            if (nw * ub > kOutBytes) nw = kOutBytes / ub;
+            block_store_bytes(obufs + (size_t)(jd % kDepth) * kOutBuf, r.out + excl * ub,
+                              (uint32_t)(nw * ub));
         }
         return true;
     };
 
-    // Thread 0 feeds the ring. The chunk it loads at the top of iteration i
-    // was claimed at the top of iteration i-1, its item index fetched in the
-    // middle and its item descriptor at the end of iteration i-1, so none of
-    // these global round trips stalls the CTA.
-    bool producing = true;   // meaningful in thread 0 only
-    uint32_t next_claim = 0, next_it = 0;
-    auto fetch_it = [&]() {
-        if (J.chunk_item && next_claim < J.total_chunks) next_it = J.chunk_item[next_claim];
-    };
-    // the descriptor of the next load, fetched asynchronously
-    auto fetch_item = [&]() {
-        if (J.items && next_claim < J.total_chunks) {
-            const uint8_t *src = reinterpret_cast<const uint8_t *>(J.items + next_it);
-            uint8_t *dst = reinterpret_cast<uint8_t *>(&s_next_item);
-#pragma unroll
-            for (int q = 0; q < (int)sizeof(Item); q += 16) cp_async16(dst + q, src + q);
-        }
-    };
-    if (tid == 0) {
-        for (int s = 0; s < kStages - 1 && producing; s++) {
-            next_claim = atomicAdd(J.claim, 1u);
-            fetch_it();
-            fetch_item();
-            producing = produce(J, next_claim, next_it, &s_next_item, s, stages, R);
-        }
-        if (producing) {   // the chunk loaded in iteration 0
-            next_claim = atomicAdd(J.claim, 1u);
-            fetch_it();
-            fetch_item();
-        }
-    }
-
-    uint32_t iter = 0, handed = 0;
+    uint32_t iter = 0;
     bool failed = false;
     while (true) {
         const int slot = iter % kStages;
-        const int p = iter % kDepth;
-        const bool ok = mbar_wait(&R.full[slot], (iter / kStages) & 1u);
-        if (cw_sync_or(!ok)) {
+        const bool okw = mbar_wait(&R.full[slot], (iter / kStages) & 1u);
+        const bool end = okw && R.end[slot] != 0;
+        const bool live = okw && !end;
+        const uint8_t *stage = stages + (size_t)slot * kStageBytes;
+        Item I{};
+        uint32_t c = 0;
+        if (live) {
+            I = R.item[slot];
+            c = R.chunk[slot];
+        }
+        const int64_t lo = I.head, hi = (int64_t)I.head + (int64_t)I.n;
+        const uint32_t k = c - I.chunk_base;
+        const bool u16 = (I.op & kOpUtf16) != 0;
+        const bool be = kAnyBE && (I.op & kOpBE);
+        bool interior;
+        int64_t vt;
+        uint32_t cnt = 0;
+        St8 s8;
+        St16 s16;
+        if (u16) {
+            const int64_t v0 = (int64_t)k * kChunk16;
+            interior = v0 - 2 >= lo && v0 + (int64_t)kChunk16 + 2 <= hi;
+            vt = v0 + (int64_t)kU16 * tid;
+            if (live) cnt = be ? chunk16_phase1<true>(s16, stage, interior, vt, lo, hi)
+                               : chunk16_phase1<false>(s16, stage, interior, vt, lo, hi);
+        } else {
+            const int64_t v0 = (int64_t)k * kChunk8;
+            interior = v0 - 4 >= lo && v0 + (int64_t)kChunk8 + 4 <= hi;
+            vt = v0 + (int64_t)kBPT * tid;
+            if (live) cnt = chunk8_phase1(s8, stage, interior, vt, lo, hi);
+        }
+        // the scan's barrier also tells every thread whether a wait gave up
+        // (here, or in thread 0's previous hand-over)
+        uint32_t agg, nfail;
+        const uint32_t t_off =
+            block_exclusive_scan_flag(cnt, !okw || failed, s_warp[iter & 1], &agg, &nfail);
+        if (nfail) {
             failed = true;
             break;
         }
-        // every compute thread is done with iteration iter-1: its stage can
-        // be refilled
-        if (tid == 0 && producing) {
-            producing = produce(J, next_claim, next_it, &s_next_item, (iter + kStages - 1) % kStages,
-                                stages, R);
-            if (producing) next_claim = atomicAdd(J.claim, 1u);   // used next iteration
+        if (end) break;
+        const int q = iter % kSlots;
+        if (tid == 0) {
+            // publish the chunk's aggregate at once (the look-backs of later
+            // chunks, in every CTA, wait for it; a chunk at the start of its
+            // item is its own inclusive prefix) and hand the count to its
+            // look-back warp
+            st_relaxed(&J.status[c], pack_status(k == 0 ? kFlagInclusive : kFlagAggregate, epoch, agg));
+            s_rec[q].agg = agg;
+            mbar_arrive(&pend_bar[q]);
         }
-        if (R.end[slot]) break;
-        const Item I = R.item[slot];
-        const uint32_t c = R.chunk[slot];
-        const uint32_t it = R.itidx[slot];
-        const uint8_t *stage = stages + (size_t)slot * kStageBytes;
-        uint8_t *obuf = obufs + (size_t)p * kOutBufBytes;
-        const int64_t lo = I.head, hi = (int64_t)I.head + (int64_t)I.n;
-        const uint32_t k = c - I.chunk_base;
-        uint32_t agg, t_off;
-        auto hand_over = [&]() {
-            if (tid == 0) {
-                st_relaxed(&J.status[c], pack_status(k == 0 ? kFlagInclusive : kFlagAggregate, epoch, agg));
-                Pending &P = s_pend[iter % kSlots];
-                P.item = I;
-                P.chunk = c;
-                P.itidx = it;
-                P.agg = agg;
-                P.end = 0;
-                mbar_arrive(&pend_bar[iter % kSlots]);
-                if (producing) fetch_it();
-            }
-            handed++;
-        };
-        if (I.op & kOpUtf16) {
-            const int64_t vt = (int64_t)k * kChunk16 + 16 * tid;
-            St16 st;
-            const uint32_t cnt = (kAnyBE && (I.op & kOpBE))
-                                     ? chunk16_phase1<true>(st, stage, vt, lo, hi)
-                                     : chunk16_phase1<false>(st, stage, vt, lo, hi);
-            t_off = block_exclusive_scan(cnt, s_warp, &agg);
-            hand_over();
-            if (iter >= kDepth && cw_sync_or(!write_out(iter - kDepth))) {
+        if (kWrite && iter >= (uint32_t)kDepth) {
+            const bool ok2 = write_out(iter - kDepth);
+            // the staging buffer is free once every thread has written it out
+            if (cw_sync_count(!ok2)) {
                 failed = true;
+                iter++;
                 break;
             }
-            chunk16_phase2<kWrite>(st, obuf, t_off, vt, lo, &s_err[p]);
+        }
+        uint8_t *obuf = obufs + (size_t)(iter % kDepth) * kOutBuf;
+        unsigned long long *err = &s_rec[q].err;
+        if (u16) {
+            if (be) chunk16_phase2<kWrite, true>(s16, stage, interior, obuf, t_off, 0, vt, lo, hi, err);
+            else chunk16_phase2<kWrite, false>(s16, stage, interior, obuf, t_off, 0, vt, lo, hi, err);
         } else {
-            const int64_t vt = (int64_t)k * kChunk8 + 32 * tid;
-            St8 st;
-            const uint32_t cnt = chunk8_phase1(st, stage, vt, lo, hi);
-            t_off = block_exclusive_scan(cnt, s_warp, &agg);
-            hand_over();
-            if (iter >= kDepth && cw_sync_or(!write_out(iter - kDepth))) {
-                failed = true;
-                break;
-            }
-            if (kAnyBE && (I.op & kOpBE))
-                chunk8_phase2<kWrite, true>(st, stage, obuf, t_off, vt, lo, hi, &s_err[p]);
-            else
-                chunk8_phase2<kWrite, false>(st, stage, obuf, t_off, vt, lo, hi, &s_err[p]);
+            uint16_t *pu = reinterpret_cast<uint16_t *>(obuf) + t_off;
+            if (be) chunk8_phase2<kWrite, true>(s8, stage, interior, pu, t_off, vt, lo, hi, err);
+            else chunk8_phase2<kWrite, false>(s8, stage, interior, pu, t_off, vt, lo, hi, err);
         }
-        // every thread read this iteration's R.item[slot] at its start: the
-        // slot's descriptor can be replaced by the one the next load needs
-        if (tid == 0 && producing) fetch_item();
+        // this warp is done with the stage
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&R.empty[slot]);
         iter++;
     }
-    // drain: write out the last kDepth chunks, then stop the look-back warp
-    for (int m = kDepth; m > 0 && !failed; m--)
-        if (iter >= (uint32_t)m && cw_sync_or(!write_out(iter - m))) failed = true;
+    // iter chunks were handed over; the end (or a failure) goes to every
+    // look-back warp as hand-overs iter .. iter + kLbWarps - 1
     if (tid == 0) {
+        for (uint32_t h = iter; h < iter + kLbWarps; h++) {
+            s_rec[h % kSlots].end = 1;
+            mbar_arrive(&pend_bar[h % kSlots]);
+        }
         if (failed) atomicOr(J.flags, 1u);
-        Pending &P = s_pend[handed % kSlots];
-        P.end = 1;
-        mbar_arrive(&pend_bar[handed % kSlots]);
+    }
+    // drain: write out the last kDepth chunks (unless any thread failed)
+    if (kWrite && cw_sync_count(failed) == 0) {
+        for (int m = kDepth; m > 0; m--) {
+            if (iter < (uint32_t)m) continue;
+            const bool ok2 = write_out(iter - m);
+            if (cw_sync_count(!ok2)) break;
+        }
     }
 }
 
@@ -1059,7 +1334,7 @@ int g_sms[64] = {0};
 
 size_t job_smem_bytes(bool write)
 {
-    return (size_t)kStages * kStageBytes + (write ? (size_t)kDepth * kOutBufBytes : 0);
+    return (size_t)kStages * kStageBytes + (write ? (size_t)kDepth * kOutBuf : 0);
 }
 
 // Every instantiation of the kernel: (write, look-back width, whether any

@@ -233,7 +233,10 @@ def test_results_do_not_depend_on_tuning(ctx, look):
     bad8 = textgen.mutate(t8.data, 2, seed=84)
     try:
         for ctas in (1, 2, 3):
-            assert gbu.gbu_set_tune(ctx, look, ctas) == gbu.GBU_OK
+            st = gbu.gbu_set_tune(ctx, look, ctas)
+            if ctas > 1 and st == gbu.GBU_INVALID_ARG:
+                break   # more CTAs per SM than fit on this device
+            assert st == gbu.GBU_OK
             t = gbu.gbu_get_tune(ctx)
             assert (t.look_width, t.ctas_per_sm) == (look, ctas)
             assert gbu.gbu_batch_plan(ctx, b.items, b.res.data_ptr(), 0) == gbu.GBU_OK

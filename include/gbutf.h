@@ -260,6 +260,27 @@ typedef struct gbu_tune {
 int32_t gbu_get_tune(gbu_ctx *ctx, gbu_tune *tune);
 int32_t gbu_set_tune(gbu_ctx *ctx, const gbu_tune *tune);
 
+/* Bounded waits. Every wait inside the kernels (for a TMA copy, for a
+ * predecessor chunk's prefix, for another warp of the CTA) gives up after
+ * `ns` nanoseconds of GPU global time (0 restores the default, 1 s). A wait
+ * that gives up makes every result of that launch GBU_DEVICE_TIMEOUT (or
+ * GBU_DEVICE_ERROR when chunks were left unprocessed); the kernel returns,
+ * the CUDA context stays usable and the next call on the context starts from
+ * clean scan state. Not part of the paper's method: failure detection of the
+ * single-pass scan. Returns GBU_OK or GBU_INVALID_ARG (ns above 60 s). Drops
+ * the context's captured batch graph. */
+int32_t gbu_set_wait_limit(gbu_ctx *ctx, uint64_t ns);
+
+/* Failure-detection test hook (not part of the paper's method). The next
+ * single-buffer launch on this context hands out its chunks starting at chunk
+ * `first_chunk` instead of 0, so chunks 0 .. first_chunk - 1 are never
+ * processed: the look-back of the chunk after them waits for their prefix
+ * until the wait limit runs out, and that launch reports GBU_DEVICE_TIMEOUT
+ * (or GBU_DEVICE_ERROR if no chunk was processed at all). Nothing faults and
+ * no wait is unbounded. One-shot; the chunk counter is written by a copy on
+ * the call's stream. Returns GBU_OK or GBU_INVALID_ARG. */
+int32_t gbu_test_skip_chunks(gbu_ctx *ctx, uint32_t first_chunk);
+
 /* Autotune the planned batch: time one warm-up and three launches of it on
  * `stream` for every (look_width, ctas_per_sm) pair, keep the pair with the
  * lowest median time on the context and store it in *chosen (may be NULL).
@@ -348,12 +369,14 @@ int32_t gbu_server_stats(gbu_server *srv, gbu_server_stats_t *stats);
  * one fixed-size device array inside this library, held by every GPU that
  * loads the library until the process exits, so inputs are limited to
  * GBU_NOALLOC_MAX_BYTES bytes (larger inputs: GBU_INVALID_ARG, nothing run).
- * The first call on a device looks up the array's device address and clears
- * it; make that first call before any stream capture. All calls share the
- * array: calls that overlap on the GPU (other streams, other host threads on
- * the same device) race and must not be issued. Same arguments, result and
- * output rules as gbu_utf8_to_utf16le; calls no cudaMalloc / cudaFree; waits
- * for `stream`. Its launches are not counted by gbu_kernel_launch_count. */
+ * The first call on a device looks up the array's device address (the array
+ * starts zeroed when the library's device code loads); make that first call
+ * before any stream capture. The call works on the current device: `stream`
+ * must belong to it (a stream of another device gives GBU_INVALID_ARG). All
+ * calls share the array: calls that overlap on the GPU (other streams, other
+ * host threads on the same device) race and must not be issued. Same
+ * arguments, result and output rules as gbu_utf8_to_utf16le; calls no
+ * cudaMalloc / cudaFree; waits for `stream`. */
 #define GBU_NOALLOC_MAX_BYTES (64ull << 20)
 gbu_result gbu_utf8_to_utf16le_noalloc(const uint8_t *d_in, uint64_t n_bytes,
                                        uint16_t *d_out, uint64_t cap_units, void *stream);

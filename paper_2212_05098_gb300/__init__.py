@@ -126,6 +126,8 @@ SIGNATURES = {
     "gbu_batch_launch_graph": (_I32, [_VP, _VP]),
     "gbu_get_tune": (_I32, [_VP, ctypes.POINTER(gbu_tune)]),
     "gbu_set_tune": (_I32, [_VP, ctypes.POINTER(gbu_tune)]),
+    "gbu_set_wait_limit": (_I32, [_VP, _U64]),
+    "gbu_test_skip_chunks": (_I32, [_VP, ctypes.c_uint32]),
     "gbu_batch_autotune": (_I32, [_VP, _VP, ctypes.c_char_p, ctypes.POINTER(gbu_tune)]),
     "gbu_server_create": (_VP, [ctypes.c_int, _U64, ctypes.c_uint32, ctypes.c_uint32]),
     "gbu_server_destroy": (None, [_VP]),
@@ -306,6 +308,14 @@ def gbu_get_tune(ctx) -> gbu_tune:
     if st != GBU_OK:
         raise RuntimeError(status_name(st))
     return t
+
+
+def gbu_set_wait_limit(ctx, ns: int) -> int:
+    return load().gbu_set_wait_limit(ctx, ns)
+
+
+def gbu_test_skip_chunks(ctx, first_chunk: int) -> int:
+    return load().gbu_test_skip_chunks(ctx, first_chunk)
 
 
 def gbu_set_tune(ctx, look_width: int, ctas_per_sm: int) -> int:

@@ -29,6 +29,15 @@ std::atomic<uint64_t> g_launches{0};
 
 constexpr uint64_t kMaxUnits = 1ull << 39;
 
+}  // namespace
+
+namespace gbu {
+// Kernel launches of every entry point (gbu_kernel_launch_count).
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace gbu
+
+namespace {
+
 gbu_result make(int32_t st, uint64_t off = 0, uint64_t len = 0)
 {
     gbu_result r;
@@ -61,6 +70,8 @@ struct gbu_ctx {
     cudaStream_t capture_stream = nullptr;
     cudaGraphExec_t graph = nullptr;
     gbu::Tune tune;                   // launch parameters of every call on the context
+    uint64_t wait_ns = 0;             // limit of the kernels' bounded waits (0: the default)
+    uint32_t skip_chunks = 0;         // test hook: the next launch starts at this chunk
     // host-buffer pipeline: copy streams, per-slice events and mapped results
     cudaStream_t h2d = nullptr, d2h = nullptr;
     cudaEvent_t ev_in[64] = {}, ev_done[64] = {};
@@ -169,6 +180,15 @@ int32_t enqueue(gbu_ctx *c, Op op, const void *in, uint64_t n, void *out, uint64
         return st;
     }
     attach_scratch(c, J);
+    J.wait_ns = c->wait_ns;
+    if (c->skip_chunks) {
+        // failure-detection hook: the launch hands out chunks from here on
+        const uint32_t from = c->skip_chunks;
+        c->skip_chunks = 0;
+        if (!ok(cudaMemcpyAsync(J.claim, &from, sizeof from, cudaMemcpyHostToDevice, stream)) ||
+            !ok(cudaStreamSynchronize(stream)))
+            return GBU_DEVICE_ERROR;
+    }
     int grid = job_grid(c->device, c->tune);
     if (grid <= 0) return GBU_DEVICE_ERROR;
     if ((uint32_t)grid > J.total_chunks) grid = (int)J.total_chunks;
@@ -749,6 +769,7 @@ static int32_t batch_enqueue(gbu_ctx *c, cudaStream_t s, bool counted = true)
     attach_scratch(c, J);
     J.item_err = c->d_item_err;
     J.item_done = c->d_item_done;
+    J.wait_ns = c->wait_ns;
     int grid = job_grid(c->device, c->tune);
     if (grid <= 0) return GBU_DEVICE_ERROR;
     if ((uint32_t)grid > J.total_chunks) grid = (int)J.total_chunks;
@@ -797,6 +818,24 @@ int32_t gbu_batch_launch_graph(gbu_ctx *c, void *stream)
     }
     if (!ok(cudaGraphLaunch(c->graph, s))) return GBU_DEVICE_ERROR;
     g_launches.fetch_add(1, std::memory_order_relaxed);   // the graph holds one kernel launch
+    return GBU_OK;
+}
+
+int32_t gbu_set_wait_limit(gbu_ctx *c, uint64_t ns)
+{
+    if (!c || ns > 60ull * 1000000000ull) return GBU_INVALID_ARG;
+    c->wait_ns = ns;
+    if (c->graph) {   // the captured launch has the old limit
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    return GBU_OK;
+}
+
+int32_t gbu_test_skip_chunks(gbu_ctx *c, uint32_t first_chunk)
+{
+    if (!c) return GBU_INVALID_ARG;
+    c->skip_chunks = first_chunk;
     return GBU_OK;
 }
 

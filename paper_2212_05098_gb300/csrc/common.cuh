@@ -82,13 +82,10 @@ constexpr uint64_t kFlagInclusive = 2;
 constexpr int kEpochShift = 40;
 constexpr uint32_t kEpochMask = (1u << 22) - 1;
 constexpr uint64_t kValueMask = (1ull << 40) - 1;
-// Bounded waits: every wait gives up after kWaitNs nanoseconds of global
-// time (1 s by default; a build knob so that a test build can make a wait run
-// out quickly), sets the timeout flag and lets the CTA finish.
-#ifndef GBU_WAIT_NS
-#define GBU_WAIT_NS 1000000000ull
-#endif
-constexpr uint64_t kWaitNs = GBU_WAIT_NS;
+// Bounded waits: every wait gives up after a limit of global time (the job's
+// wait_ns; kWaitNs when it is 0), sets the timeout flag and lets the CTA
+// finish.
+constexpr uint64_t kWaitNs = 1000000000ull;   // 1 s
 // An mbarrier wait suspends the thread in hardware until the phase completes
 // or this many nanoseconds pass, then checks the clock and waits again.
 constexpr uint32_t kSuspendNs = 20000;
@@ -151,6 +148,7 @@ struct Job {
     unsigned long long *item_err;   // [num_items] (position << 8) | kind of the first error, ~0 if none
     unsigned int *item_done;        // [num_items] chunks written
     uint32_t validate;              // 1: validation only (no look-back; out_len reported as 0)
+    uint64_t wait_ns;               // limit of every bounded wait (0: kWaitNs)
 };
 
 __device__ __forceinline__ uint64_t ld_relaxed(const unsigned long long *p)
@@ -296,76 +294,6 @@ __device__ __forceinline__ uint64_t lookback_window(const uint64_t (&w)[kLook], 
     *ready = rd;
     *found = fd;
     return part;
-}
-
-// Decoupled look-back, run by one full warp for the item chunk `k` (k > 0)
-// whose status words start at `status` (the item's first chunk). Each round
-// reads kLook words per lane (the 32 * kLook nearest predecessors
-// not yet summed) in one L2 round trip, sums aggregates back to the nearest
-// inclusive prefix, and moves on if there is none. Returns the chunk's
-// exclusive prefix (all lanes). On a wait longer than kWaitNs, or as soon as
-// another CTA of the launch gave up, it sets the timeout flag and returns what
-// it has.
-// kLook is a tuning parameter (see Tune in kernels.h).
-template <int kLook>
-__device__ __forceinline__ uint64_t lookback(const unsigned long long *status, uint32_t k,
-                                             uint32_t epoch, unsigned int *flags)
-{
-    const int lane = threadIdx.x & 31;
-    // before the item's first chunk: an inclusive prefix of 0
-    const uint64_t start = pack_status(kFlagInclusive, epoch, 0);
-    uint64_t excl = 0;
-    int64_t base = (int64_t)k - 1;
-    uint32_t rounds = 0;
-    uint64_t t0 = 0;
-    while (true) {
-        // one round trip for the whole window, then one pass over it from the
-        // nearest predecessor backwards (only the raw words stay in registers)
-        uint64_t w[kLook];
-#pragma unroll
-        for (int m = 0; m < kLook; m++) {
-            const int64_t idx = base - 32 * m - lane;
-            w[m] = idx >= 0 ? ld_relaxed(&status[idx]) : start;
-        }
-        bool ready = true, found = false;
-        uint64_t part = 0;
-#pragma unroll
-        for (int m = 0; m < kLook; m++) {
-            if (found) break;                        // warp-uniform
-            const uint64_t x = w[m];
-            const bool current = ((x >> kEpochShift) & kEpochMask) == epoch;
-            const uint64_t flag = current ? x >> 62 : 0;
-            const uint32_t inc = __ballot_sync(kFull, flag == kFlagInclusive);
-            const uint32_t nr = __ballot_sync(kFull, flag == 0);
-            // ready when no word before the nearest inclusive one is missing
-            const uint32_t upto = inc ? ((inc & (0u - inc)) - 1u) : 0xFFFFFFFFu;
-            if (nr & upto) ready = false;
-            const uint64_t v = x & kValueMask;
-            if (inc) {
-                const int l = __ffs(inc) - 1;          // nearest predecessor with a full prefix
-                if (lane <= l) part += v;
-                found = true;
-            } else {
-                part += v;
-            }
-        }
-        if (ready) {
-            excl += warp_sum_u64(part);
-            if (found) return excl;
-            base -= 32 * kLook;
-            continue;
-        }
-        ++rounds;
-        if (rounds == 1) t0 = globaltimer_ns();
-        const bool other = (rounds & 15u) == 0 &&
-                           (*reinterpret_cast<volatile unsigned int *>(flags) != 0 ||
-                            globaltimer_ns() - t0 > kWaitNs);
-        if (__any_sync(kFull, other)) {
-            if (lane == 0) atomicOr(flags, 1u);
-            return excl;
-        }
-        if (rounds > 3) __nanosleep(rounds < 16 ? GBU_LB_SLEEP_SHORT : GBU_LB_SLEEP_LONG);
-    }
 }
 
 // The aligned middle part of block_store_bytes for a source offset of Q
@@ -539,14 +467,14 @@ __device__ __forceinline__ bool mbar_try_wait_hint(uint64_t *bar, uint32_t parit
 }
 
 // Bounded wait for a phase of an mbarrier; false when the wait gave up
-// (after kWaitNs of global time).
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+// (after limit_ns of global time).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer_ns();
     do {
         if (mbar_try_wait_hint(bar, parity, kSuspendNs)) return true;
-    } while (globaltimer_ns() - t0 < kWaitNs);
+    } while (globaltimer_ns() - t0 < limit_ns);
     return false;
 }
 

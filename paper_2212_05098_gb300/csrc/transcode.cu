@@ -1018,6 +1018,7 @@ transcode_kernel(const Job J)
     }
     __syncthreads();
     const uint32_t epoch = s_epoch;
+    const uint64_t wlim = J.wait_ns ? J.wait_ns : kWaitNs;   // limit of every bounded wait
 
     if (tid >= kThreads + 32 * kLbWarps) {
         // ---- producer warp (lane 0): refill the ring, account for chunks ----
@@ -1040,8 +1041,8 @@ transcode_kernel(const Job J)
         // by its last CTA); then refill the stage
         uint32_t j = 0;
         for (; producing || j + 1 < np; j++) {
-            if (!mbar_wait(&R.empty[j % kStages], (j / kStages) & 1u) ||
-                !mbar_wait(&excl_bar[j % kSlots], (j / kSlots) & 1u)) {
+            if (!mbar_wait(&R.empty[j % kStages], (j / kStages) & 1u, wlim) ||
+                !mbar_wait(&excl_bar[j % kSlots], (j / kSlots) & 1u, wlim)) {
                 ok = false;
                 break;
             }
@@ -1066,7 +1067,7 @@ transcode_kernel(const Job J)
                 // kClaim 2: claim the chunk only once its predecessor in the
                 // CTA's sequence is counted, so that chunks are claimed just
                 // ahead of their processing
-                if (kClaim == 2 && !mbar_wait(&pend_bar[(np - 1) % kSlots], ((np - 1) / kSlots) & 1u)) {
+                if (kClaim == 2 && !mbar_wait(&pend_bar[(np - 1) % kSlots], ((np - 1) / kSlots) & 1u, wlim)) {
                     ok = false;
                     break;
                 }
@@ -1078,7 +1079,7 @@ transcode_kernel(const Job J)
         }
         if (!ok) atomicOr(J.flags, 1u);
         // the look-back warps are done (every inclusive prefix is out)
-        if (!mbar_wait(&lb_exit, 0)) atomicOr(J.flags, 1u);
+        if (!mbar_wait(&lb_exit, 0, wlim)) atomicOr(J.flags, 1u);
         exit_job(J, epoch, j);
         return;
     }
@@ -1120,7 +1121,7 @@ transcode_kernel(const Job J)
             while (!ending && __popc(live) < kSl) {
                 const int q = next % kSlots;
                 const uint32_t par = (next / kSlots) & 1u;
-                const bool ready = live == 0 ? __all_sync(kFull, mbar_wait(&pend_bar[q], par))
+                const bool ready = live == 0 ? __all_sync(kFull, mbar_wait(&pend_bar[q], par, wlim))
                                              : __all_sync(kFull, mbar_test(&pend_bar[q], par));
                 if (!ready) {
                     if (live == 0) failed = true;
@@ -1190,11 +1191,11 @@ transcode_kernel(const Job J)
                 // back off while predecessors are late (the first rounds
                 // re-read at once: an L2 round trip paces them)
                 if (++idle_rounds > 2) __nanosleep(idle_rounds < 16 ? GBU_LB_SLEEP_SHORT : GBU_LB_SLEEP_LONG);
-                // predecessors not ready: give up after kWaitNs without
+                // predecessors not ready: give up after the wait limit without
                 // progress, or as soon as another CTA of the launch gave up
                 const uint64_t now = globaltimer_ns();
                 if (t_idle == 0) t_idle = now;
-                const bool stop = now - t_idle > kWaitNs ||
+                const bool stop = now - t_idle > wlim ||
                                   *reinterpret_cast<volatile unsigned int *>(J.flags) != 0;
                 if (__any_sync(kFull, stop)) {
                     failed = true;
@@ -1214,7 +1215,7 @@ transcode_kernel(const Job J)
     // false if the wait for the offset gave up
     auto write_out = [&](uint32_t jd) -> bool {
         const int q = jd % kSlots;
-        if (!mbar_wait(&excl_bar[q], (jd / kSlots) & 1u)) return false;
+        if (!mbar_wait(&excl_bar[q], (jd / kSlots) & 1u, wlim)) return false;
         const ChunkRec &r = s_rec[q];
         const uint64_t excl = r.excl;
         if (excl < r.cap) {
@@ -1233,7 +1234,7 @@ transcode_kernel(const Job J)
     bool failed = false;
     while (true) {
         const int slot = iter % kStages;
-        const bool okw = mbar_wait(&R.full[slot], (iter / kStages) & 1u);
+        const bool okw = mbar_wait(&R.full[slot], (iter / kStages) & 1u, wlim);
         const bool end = okw && R.end[slot] != 0;
         const bool live = okw && !end;
         const uint8_t *stage = stages + (size_t)slot * kStageBytes;

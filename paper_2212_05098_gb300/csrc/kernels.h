@@ -49,4 +49,7 @@ cudaError_t launch_job(const Job &J, bool write, int grid, cudaStream_t stream,
 cudaError_t launch_write_result(ResultSlot *dst, int32_t status, uint64_t in_offset,
                                 uint64_t out_len, cudaStream_t stream);
 
+// Count one kernel launch (gbu_kernel_launch_count).
+void note_launch();
+
 }  // namespace gbu

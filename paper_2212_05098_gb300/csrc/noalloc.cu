@@ -16,8 +16,10 @@
 // In host code the array's name only stands in for the symbol; it is not a
 // device address. Its device address is looked up with cudaGetSymbolAddress
 // once per device, with that device current, on the first call made on that
-// device; that first call also clears the array. Make that first call before
-// any stream capture.
+// device; make that first call before any stream capture. The array has no
+// initializer, so it is zero when the library's device code is loaded: the
+// look-back status words start "not ready" and the kernel keeps their epoch
+// from call to call; each call clears the counters it needs zero.
 #include <cstring>
 #include <mutex>
 
@@ -68,6 +70,13 @@ extern "C" gbu_result gbu_utf8_to_utf16le_noalloc(const uint8_t *d_in, uint64_t 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
         return fail(GBU_DEVICE_ERROR);
+    // the array used is the current device's: the stream must belong to it
+    // (checked before anything is enqueued)
+    if (s) {
+        int sdev = -1;
+        if (cudaStreamGetDevice(s, &sdev) != cudaSuccess) return fail(GBU_INVALID_ARG);
+        if (sdev != dev) return fail(GBU_INVALID_ARG);
+    }
 
     Job J{};
     J.item0 = make_item(d_in, n_bytes, false, d_out, cap_units, true, nullptr, 0);
@@ -85,9 +94,6 @@ extern "C" gbu_result gbu_utf8_to_utf16le_noalloc(const uint8_t *d_in, uint64_t 
             void *p = nullptr;
             if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p)
                 return fail(GBU_DEVICE_ERROR);
-            // status words must start "not ready"; the kernel keeps the epoch
-            if (cudaMemsetAsync(p, 0, kScratchBytes, s) != cudaSuccess)
-                return fail(GBU_DEVICE_ERROR);
             d.base = static_cast<unsigned char *>(p);
         }
         base = d.base;
@@ -95,7 +101,8 @@ extern "C" gbu_result gbu_utf8_to_utf16le_noalloc(const uint8_t *d_in, uint64_t 
     // The array keeps whatever the previous call left: counters and flags must
     // start at zero and the first-error word at all ones.
     if (cudaMemsetAsync(base, 0, 16, s) != cudaSuccess ||
-        cudaMemsetAsync(base + 16, 0xFF, 8, s) != cudaSuccess)
+        cudaMemsetAsync(base + 16, 0xFF, 8, s) != cudaSuccess ||
+        cudaMemsetAsync(base + kHdrClaim, 0, 4, s) != cudaSuccess)
         return fail(GBU_DEVICE_ERROR);
 
     J.chunks_done = reinterpret_cast<unsigned int *>(base + kHdrChunks);
@@ -112,6 +119,7 @@ extern "C" gbu_result gbu_utf8_to_utf16le_noalloc(const uint8_t *d_in, uint64_t 
     J.item0.result = reinterpret_cast<ResultSlot *>(base + kHdrResult);
     const int grid = (uint32_t)max_grid > J.total_chunks ? (int)J.total_chunks : max_grid;
     if (launch_job(J, true, grid, s) != cudaSuccess) return fail(GBU_DEVICE_ERROR);
+    note_launch();
     gbu_result r;
     if (cudaMemcpyAsync(&r, base + kHdrResult, sizeof r, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)

@@ -67,12 +67,15 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=256 << 20,
                     help="bytes of each buffer the oracle baseline transcodes")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["single", "batched", "serving", "latency"],
+    ap.add_argument("--workload", choices=["single", "batched", "serving", "latency", "split"],
                     default="single",
-                    help="single: 4 profiles x 2 directions x one buffer each (default); "
+                    help="single: 4 profiles x 2 directions x one buffer each (default; the line "
+                         "also carries reduced batched, serving and UTF-32 measurements); "
                          "batched: many strings in one persistent graph-captured launch; "
                          "serving: Poisson request arrivals through the serving loop; "
-                         "latency: one call's latency and throughput against input size")
+                         "latency: one call's latency and throughput against input size; "
+                         "split: every buffer cut across the ranks at character boundaries, "
+                         "one all-gather of a 32-byte record per rank")
     ap.add_argument("--strings", type=int, default=200_000, help="batched: number of strings")
     ap.add_argument("--rates", default="0.1,0.25,0.5,0.75,0.9,1.0,1.2",
                     help="serving: arrival rates as fractions of the plain kernel's GB/s")
@@ -84,7 +87,34 @@ def parse():
                     help="batched: scale the string lengths so that they add up to this many "
                          "bytes (0: unscaled, log-uniform 16 B - 1 MiB)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-strings", type=int, default=20_000,
+                    help="single: strings of the batched measurement in the default line")
+    ap.add_argument("--serve-rates", default="0.1,0.25,0.5,0.75,1.0",
+                    help="single: load fractions of the serving measurement in the default line")
+    ap.add_argument("--serve-window", type=float, default=0.25,
+                    help="single: arrival window per load of the serving measurement (seconds)")
+    ap.add_argument("--utf32-size", type=int, default=256 << 20,
+                    help="single: UTF-8 bytes per profile for the UTF-32 measurement (0: skip)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="single: skip the batched, serving and UTF-32 measurements")
     return ap.parse_args()
+
+
+def launcher_cmd(argv: list[str], gpus: int, port: int) -> list[str]:
+    """The command that runs this benchmark as `gpus` ranks on this node (one
+    process per GPU, rendezvous on 127.0.0.1) with the same arguments."""
+    return [sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+            f"--nproc-per-node={gpus}", "--master-addr=127.0.0.1", f"--master-port={port}",
+            os.path.abspath(__file__), *argv]
+
+
+def free_port() -> int:
+    import socket
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
 
 
 def dist_env():
@@ -341,6 +371,9 @@ def run_reference(args, rank, world):
 
 def main():
     args = parse()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        # started as `bench.py --gpus N`: start the N ranks ourselves
+        sys.exit(subprocess.call(launcher_cmd(sys.argv[1:], args.gpus, free_port())))
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
@@ -353,6 +386,9 @@ def main():
         return
     if args.workload == "latency":
         run_latency(args, rank, world, local)
+        return
+    if args.workload == "split":
+        run_split(args, rank, world, local)
         return
     # process pool for the generator: started before the first CUDA call
     pool = textgen.process_pool() if args.size >= (64 << 20) else None
@@ -539,6 +575,30 @@ def main():
     stream.synchronize()
     validate_gbs = 3 * bytes_step / (e0.elapsed_time(e1) / 1e3) / 1e9
 
+    # ---- the batched launch, the serving loop and UTF-32 on the same device --
+    extras = {}
+    if not args.no_extras and world == 1:
+        plain_gbs = value / world
+        if args.batch_strings > 0:
+            b = batched_section(gbu, torch, local, cases, [c["d_in"] for c in cases],
+                                args.batch_strings, 4, stream, plain_gbs, 20, 3, 1)
+            b.pop("_lay"), b.pop("_is16")
+            b["workload"] = (f"{b['strings']} strings (reduced from 200000), lengths log-uniform "
+                             "16 B-1 MiB, profiles uniform, direction 50/50, windows of the "
+                             "buffers above; one graph-captured launch per step, 20 steps")
+            extras["batched"] = b
+        rates = [float(x) for x in args.serve_rates.split(",") if x]
+        if rates:
+            sv = serving_section(gbu, torch, local, cases, [c["d_in"] for c in cases], rates,
+                                 args.serve_window, plain_gbs, 8 << 30, 2, 5, min_requests=1000)
+            sv["workload"] = (f"Poisson arrivals over {args.serve_window} s per load, sizes "
+                              "log-uniform 64 B-16 MiB, 1 % injected errors, windows of the "
+                              "buffers above; loads are fractions of this run's value")
+            extras["serving"] = sv
+        if args.utf32_size > 0:
+            extras["utf32"] = utf32_section(gbu, torch, ctx, args.utf32_size, stream,
+                                            roofline["frac"])
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         b, dt = cpu_baseline(cases, args.cpu_sample)
@@ -569,9 +629,194 @@ def main():
             "directions": directions,
             "per_buffer_input_gbs": per_case,
             "validate_only_input_gbs": validate_gbs,
+            **extras,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clocks,
+            "gpu_launches": launches,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def utf32_section(gbu, torch, ctx, size, stream, utf16_frac):
+    """UTF-8 <-> UTF-32LE on the two profiles that carry multi-byte
+    characters (cjk, emoji), `size` UTF-8 bytes each: per direction the
+    median of 5 calls (CUDA events on the call's stream), the roofline
+    fraction (input + output bytes) and its ratio to the UTF-16 kernel's
+    fraction `utf16_frac` measured in the same run."""
+    peak, _ = measured_peak()
+    sh = stream.cuda_stream
+    out = {}
+    for prof in ("cjk", "emoji"):
+        t = textgen.generate(prof, size, textgen.UTF8, seed=textgen.PROFILE_SEED[prof],
+                             keep_lens=False)
+        u8 = t.data
+        u32 = np.ascontiguousarray(t.cps, dtype="<u4")
+        d8 = torch.from_numpy(u8).cuda()
+        d32 = torch.from_numpy(u32.view(np.uint8)).cuda()
+        o32 = torch.empty(4 * u8.size, dtype=torch.uint8, device="cuda")
+        o8 = torch.empty(4 * u32.size, dtype=torch.uint8, device="cuda")
+        calls = {
+            "utf8_to_utf32le": (lambda: gbu.gbu_utf8_to_utf32le(
+                ctx.handle, d8.data_ptr(), u8.size, o32.data_ptr(), u8.size, sh), u8.size, 4),
+            "utf32le_to_utf8": (lambda: gbu.gbu_utf32le_to_utf8(
+                ctx.handle, d32.data_ptr(), u32.size, o8.data_ptr(), 4 * u32.size, sh),
+                4 * u32.size, 1),
+        }
+        for name, (call, in_bytes, ub) in calls.items():
+            r = call()
+            want = u32.size if name == "utf8_to_utf32le" else u8.size
+            if r.status != gbu.GBU_OK or r.out_len != want:
+                raise RuntimeError(f"utf32 {prof} {name}: {r}")
+            ms = []
+            for _ in range(5):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                call()
+                e1.record(stream)
+                stream.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            m = statistics.median(ms)
+            alg = in_bytes + ub * r.out_len
+            frac = alg / (m / 1e3) / 1e9 / peak
+            out[f"{prof}/{name}"] = {"input_gbs": in_bytes / (m / 1e3) / 1e9, "ms": m,
+                                     "alg_bytes": alg, "frac": frac,
+                                     "frac_over_utf16_frac": frac / utf16_frac}
+        del d8, d32, o32, o8
+    out["size_utf8_bytes"] = size
+    out["frac_over_utf16_frac_mean"] = float(np.mean(
+        [v["frac_over_utf16_frac"] for k, v in out.items() if isinstance(v, dict)]))
+    return out
+
+
+SPLIT_METRIC = ("input GB/s, validated UTF-8<->UTF-16LE transcoding, every 1 GiB buffer cut "
+                "across the ranks at character boundaries (4 profiles x 2 directions)")
+
+
+def run_split(args, rank, world, local):
+    """Split workload: every rank holds the same 8 buffers (4 profiles x 2
+    directions) and converts its part of each, cut at character boundaries;
+    one step = the 8 part launches plus one all-gather (NCCL) of the 8
+    result records (32 bytes each) per rank, from which every rank knows its
+    output offsets and the buffers' results. Total work is fixed as ranks are
+    added (strong scaling)."""
+    pool = textgen.process_pool() if args.size >= (64 << 20) else None
+    import torch
+    import torch.distributed as dist
+
+    import paper_2212_05098_gb300 as gbu
+    from paper_2212_05098_gb300 import shard
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    profiles = args.profiles.split(",")
+    cases = gen_inputs(profiles, args.size, 0, pool)    # identical buffers on every rank
+    if pool is not None:
+        pool.shutdown()
+    gbu.load()
+    ctx = gbu.Context(local)
+    ctx.reserve(args.size)
+    stream = torch.cuda.Stream()
+    sh = stream.cuda_stream
+    results = torch.zeros((len(cases), 4), dtype=torch.int64, device="cuda")
+    for i, c in enumerate(cases):
+        u16 = c["dir"] == "utf16le_to_utf8"
+        cuts = shard.split_points(c["data"], world, u16)
+        part = c["data"][cuts[rank]:cuts[rank + 1]]
+        c["part_units"] = part.size // 2 if u16 else part.size
+        c["d_in"] = torch.from_numpy(np.array(part, copy=True)).cuda()
+        c["cap"] = 3 * c["part_units"] if u16 else c["part_units"]
+        c["d_out"] = torch.empty(max(1, c["cap"] * (1 if u16 else 2)), dtype=torch.uint8,
+                                 device="cuda")
+        c["res"] = results[i].data_ptr()
+    gathered = torch.zeros((world, len(cases), 4), dtype=torch.int64, device="cuda")
+
+    def step():
+        for c in cases:
+            f = (gbu.gbu_utf16le_to_utf8_async if c["dir"] == "utf16le_to_utf8"
+                 else gbu.gbu_utf8_to_utf16le_async)
+            st = f(ctx.handle, c["d_in"].data_ptr() if c["part_units"] else 0, c["part_units"],
+                   c["d_out"].data_ptr(), c["cap"], c["res"], sh)
+            if st != gbu.GBU_OK:
+                raise RuntimeError(f"enqueue failed: {gbu.status_name(st)}")
+        if world > 1:
+            with torch.cuda.stream(stream):
+                dist.all_gather_into_tensor(gathered, results)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    stream.synchronize()
+    # combine the ranks' records and check them against one whole-buffer call
+    rows = gathered.cpu().numpy() if world > 1 else results.cpu().numpy()[None]
+    units = [[c["part_units"] for c in cases]]
+    if world > 1:
+        u = torch.tensor(units[0], dtype=torch.int64, device="cuda")
+        ug = torch.zeros((world, len(cases)), dtype=torch.int64, device="cuda")
+        dist.all_gather_into_tensor(ug, u)
+        units = ug.cpu().tolist()
+    whole_ctx = gbu.Context(local)
+    for i, c in enumerate(cases):
+        parts = [shard.PartResult(int(rows[r, i, 0]) & 0xFFFFFFFF, int(rows[r, i, 1]),
+                                  int(rows[r, i, 2])) for r in range(world)]
+        _, total = shard.combine(parts, [units[r][i] for r in range(world)])
+        if rank == 0:
+            d = torch.from_numpy(c["data"]).cuda()
+            o = torch.empty(2 * c["data"].size, dtype=torch.uint8, device="cuda")
+            if c["dir"] == "utf8_to_utf16le":
+                w = gbu.gbu_utf8_to_utf16le(whole_ctx.handle, d.data_ptr(), d.numel(),
+                                            o.data_ptr(), d.numel(), sh)
+            else:
+                w = gbu.gbu_utf16le_to_utf8(whole_ctx.handle, d.data_ptr(), d.numel() // 2,
+                                            o.data_ptr(), 3 * (d.numel() // 2), sh)
+            if (w.status, w.in_offset, w.out_len) != (total.status, total.in_offset,
+                                                      total.out_len):
+                raise RuntimeError(f"split result {total} != whole-buffer result {w}")
+            del d, o
+    whole_ctx.close()
+    torch.cuda.empty_cache()
+
+    sampler = ClockSampler(local)
+    K = args.steps
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    n0 = gbu.gbu_kernel_launch_count()
+    t_wall0 = time.time()
+    start.record(stream)
+    for _ in range(K):
+        step()
+    end.record(stream)
+    stream.synchronize()
+    t_wall1 = time.time()
+    launches = gbu.gbu_kernel_launch_count() - n0
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.stop()
+    clocks = sampler.summary(t_wall0, t_wall1)
+    whole = sum(c["data"].size for c in cases) * K
+    # every rank converts 1/world of each buffer: the job's bytes are the
+    # whole buffers once, over the slowest rank's time
+    _, ms = job_rate(0.0, start.elapsed_time(end), world, "cuda")
+    value = whole / (ms / 1e3) / 1e9
+    if rank == 0:
+        line = {
+            "metric": SPLIT_METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
+            "steps": K, "warmup": max(3, args.warmup), "ms_per_step": ms / K,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+            "dtype": "u8+u16", "data": "synthetic (seeded i.i.d. code points per profile)",
+            "config": {"workload": f"8 buffers of {args.size} B, each cut into {world} parts "
+                                   "at character boundaries",
+                       "bytes_per_buffer": args.size, "buffers": len(cases),
+                       "parallelism": f"split x {world}, one all-gather of 8 x 32 B per rank "
+                                      "per step" if world > 1 else "one rank, no exchange",
+                       "l2": "inputs larger than the 129 MB L2; no flush"},
+            "cpu_baseline": None, "e2e": None, "clocks": clocks,
             "gpu_launches": launches,
         }
         print(json.dumps(line), flush=True)
@@ -584,37 +829,22 @@ BATCH_METRIC = ("input GB/s, validated UTF-8<->UTF-16LE transcoding of many stri
                 "persistent graph-captured launch")
 
 
-def run_batched(args, rank, world, local):
-    """Batched workload: `--strings` independent strings, lengths log-uniform
-    over 16 B - 1 MiB (optionally scaled to `--batch-total` bytes), profile
-    uniform over the four, direction 50/50, each a window of that profile's
-    corpus (`--size` bytes per profile and encoding) cut at character
-    boundaries. One step = one launch of the autotuned batch (CUDA graph).
-    Also timed in the same run: the same strings as one plain-kernel launch
-    each, and the plain single-buffer kernel on the corpora themselves."""
+def batched_section(gbu, torch, local, cases, d_corp, n_strings, seed, stream, plain_gbs,
+                    steps, warmup, world, batch_total=0, per_string=True):
+    """The batched form (one persistent graph-captured launch over many
+    strings) on windows of the resident corpora `d_corp` (one per case):
+    `n_strings` strings, lengths log-uniform over 16 B - 1 MiB (scaled to
+    `batch_total` bytes if given), profile uniform, direction 50/50. Plans,
+    autotunes and times `steps` graph launches; `plain_gbs` is the plain
+    single-buffer kernel's input GB/s in the same run."""
     from textgen import batch as tbatch
-    pool = textgen.process_pool()
-    import torch
-    import torch.distributed as dist
-
-    import paper_2212_05098_gb300 as gbu
-
-    torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl")
-    profiles = args.profiles.split(",")
-    cases = gen_inputs(profiles, args.size, rank, pool)
-    pool.shutdown()
     corpora = [(c["profile"], textgen.UTF8 if c["dir"] == "utf8_to_utf16le" else textgen.UTF16,
                 c["data"]) for c in cases]
-    lay = tbatch.layout(corpora, args.strings, 16, 1 << 20, seed=4 + 1000 * rank)
-    if args.batch_total:
-        lay = tbatch.layout(corpora, args.strings, 16, 1 << 20, seed=4 + 1000 * rank,
-                            scale=args.batch_total / lay.total_bytes)
+    lay = tbatch.layout(corpora, n_strings, 16, 1 << 20, seed=seed)
+    if batch_total:
+        lay = tbatch.layout(corpora, n_strings, 16, 1 << 20, seed=seed,
+                            scale=batch_total / lay.total_bytes)
     n_str = lay.nbytes.size
-
-    gbu.load()
-    d_corp = [torch.from_numpy(c["data"]).cuda() for c in cases]
     is16 = np.array([corpora[k][1] == textgen.UTF16 for k in lay.corpus])
     cap_bytes = np.where(is16, 3 * (lay.nbytes // 2), 2 * lay.nbytes)
     out_off = np.zeros(n_str + 1, dtype=np.int64)
@@ -635,7 +865,6 @@ def run_batched(args, rank, world, local):
             items.append((inp if n else 0, n, base_out + int(out_off[i]), n,
                           gbu.GBU_OP_UTF8_TO_UTF16LE))
     ctx = gbu.Context(local)
-    stream = torch.cuda.Stream()
     sh = stream.cuda_stream
     st = gbu.gbu_batch_plan(ctx.handle, items, d_res.data_ptr(), sh)
     if st != gbu.GBU_OK:
@@ -646,7 +875,7 @@ def run_batched(args, rank, world, local):
     t_tune = time.perf_counter() - t_tune0
     if st != gbu.GBU_OK:
         raise RuntimeError(f"autotune: {gbu.status_name(st)}")
-    for _ in range(max(3, args.warmup)):
+    for _ in range(max(3, warmup)):
         if gbu.gbu_batch_launch_graph(ctx.handle, sh) != gbu.GBU_OK:
             raise RuntimeError("batch launch failed")
     stream.synchronize()
@@ -657,202 +886,79 @@ def run_batched(args, rank, world, local):
         raise RuntimeError(f"string {i}: {gbu.status_name(int(res['status'][i]))}")
     in_bytes = int(lay.nbytes.sum())
     out_bytes = int((res["len"] * np.where(is16, 1, 2)).sum())
-
-    K = args.steps
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(K)]
-    sampler = ClockSampler(local)
-    if world > 1:
-        dist.barrier()
+          for _ in range(steps)]
     torch.cuda.synchronize()
     n0 = gbu.gbu_kernel_launch_count()
-    t_wall0 = time.time()
-    for k in range(K):
+    for k in range(steps):
         ev[k][0].record(stream)
         gbu.gbu_batch_launch_graph(ctx.handle, sh)
         ev[k][1].record(stream)
     stream.synchronize()
-    t_wall1 = time.time()
     launches = gbu.gbu_kernel_launch_count() - n0
-    sampler.stop()
-    clocks = sampler.summary(t_wall0, t_wall1)
-    ms_list = [a.elapsed_time(b) for a, b in ev]
-    value, ms_total = job_rate(in_bytes * K, sum(ms_list), world, "cuda")
+    ms_list = [x.elapsed_time(y) for x, y in ev]
+    value, ms_total = job_rate(in_bytes * steps, sum(ms_list), world, "cuda")
+    out = {"value": value, "unit": "GB/s", "strings": n_str, "input_bytes": in_bytes,
+           "output_bytes": out_bytes, "ms_per_launch": ms_total / steps,
+           "p50_launch_ms": float(np.percentile(ms_list, 50)),
+           "p99_launch_ms": float(np.percentile(ms_list, 99)),
+           "tune": {"look_width": tune.look_width, "ctas_per_sm": tune.ctas_per_sm,
+                    "autotune_s": round(t_tune, 3)},
+           "plain_single_buffer_gbs": plain_gbs,
+           "plain_over_batched": plain_gbs / (value / world),
+           "frac": (in_bytes + out_bytes) / (ms_total / steps / 1e3) / 1e9 / measured_peak()[0],
+           "launches": launches}
+    if per_string:
+        # the same strings, one plain-kernel launch each
+        plain = gbu.Context(local)
+        plain.reserve(1 << 20)
+        res1 = torch.zeros(4, dtype=torch.int64, device="cuda")
+        r1 = res1.data_ptr()
 
-    # the same strings, one plain-kernel launch each (default launch parameters)
-    plain = gbu.Context(local)
-    plain.reserve(1 << 20)
-    res1 = torch.zeros(4, dtype=torch.int64, device="cuda")
-    r1 = res1.data_ptr()
+        def one_by_one():
+            for (inp, n, outp, cap, op) in items:
+                if op == gbu.GBU_OP_UTF8_TO_UTF16LE:
+                    gbu.gbu_utf8_to_utf16le_async(plain.handle, inp, n, outp, cap, r1, sh)
+                else:
+                    gbu.gbu_utf16le_to_utf8_async(plain.handle, inp, n, outp, cap, r1, sh)
 
-    def per_string():
-        for (inp, n, outp, cap, op) in items:
-            if op == gbu.GBU_OP_UTF8_TO_UTF16LE:
-                gbu.gbu_utf8_to_utf16le_async(plain.handle, inp, n, outp, cap, r1, sh)
-            else:
-                gbu.gbu_utf16le_to_utf8_async(plain.handle, inp, n, outp, cap, r1, sh)
-
-    per_string()
-    stream.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t0 = time.perf_counter()
-    e0.record(stream)
-    per_string()
-    e1.record(stream)
-    stream.synchronize()
-    ps_wall = time.perf_counter() - t0
-    ps_ms = e0.elapsed_time(e1)
-
-    # the plain single-buffer kernel on the corpora (same GPU, same run)
-    def single():
-        for c, d in zip(cases, d_corp):
-            if c["dir"] == "utf8_to_utf16le":
-                gbu.gbu_utf8_to_utf16le_async(plain.handle, d.data_ptr(), d.numel(),
-                                              d_out.data_ptr(), d.numel(), r1, sh)
-            else:
-                gbu.gbu_utf16le_to_utf8_async(plain.handle, d.data_ptr(), d.numel() // 2,
-                                              d_out.data_ptr(), 3 * (d.numel() // 2), r1, sh)
-
-    plain.reserve(args.size)
-    single()
-    e0.record(stream)
-    for _ in range(3):
-        single()
-    e1.record(stream)
-    stream.synchronize()
-    single_gbs = 3 * sum(d.numel() for d in d_corp) / (e0.elapsed_time(e1) / 1e3) / 1e9
-
-    peak, peak_src = measured_peak()
-    ms_launch = ms_total / K
-    roofline = {"kernel": KERNEL, "bound": "hbm",
-                "achieved": (in_bytes + out_bytes) / (ms_launch / 1e3) / 1e9, "peak": peak,
-                "unit": "GB/s", "frac": (in_bytes + out_bytes) / (ms_launch / 1e3) / 1e9 / peak,
-                "traffic": None, "peak_source": peak_src,
-                "algorithmic_bytes_per_launch": in_bytes + out_bytes, "avg_launch_ms": ms_launch}
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import oracle
-        budget, done, t_c = args.cpu_sample, 0, 0.0
-        for i in range(n_str):
-            if done >= budget:
-                break
-            d = cases[int(lay.corpus[i])]["data"][int(lay.start[i]):int(lay.start[i] + lay.nbytes[i])]
-            t0 = time.perf_counter()
-            if is16[i]:
-                oracle.utf16le_to_utf8(d)
-            else:
-                oracle.utf8_to_utf16le(d)
-            t_c += time.perf_counter() - t0
-            done += d.size
-        cpu = {"value": done / t_c / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
-               "sample": f"oracle (scalar C, 1 thread) on the first strings of the batch, "
-                         f"{done / 1e9:.2f} GB, {t_c:.1f} s"}
-    if rank == 0:
-        line = {
-            "metric": BATCH_METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
-            "steps": K, "warmup": max(3, args.warmup), "ms_per_step": ms_total / K,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "u8+u16", "data": "synthetic (windows of seeded per-profile corpora)",
-            "config": {"workload": f"{n_str} strings, lengths log-uniform 16 B-1 MiB"
-                                   + (f" scaled to {args.batch_total} B total" if args.batch_total
-                                      else "")
-                                   + ", profiles uniform over 4, direction 50/50",
-                       "strings": n_str, "input_bytes": in_bytes, "output_bytes": out_bytes,
-                       "corpus_bytes_per_profile_and_encoding": args.size,
-                       "tune": {"look_width": tune.look_width, "ctas_per_sm": tune.ctas_per_sm,
-                                "autotune_s": round(t_tune, 3)},
-                       "l2": "inputs read once per step from 8 corpora of "
-                             f"{args.size >> 20} MiB; no flush"},
-            "roofline": roofline,
-            "per_string_launches": {"value": in_bytes / (ps_ms / 1e3) / 1e9, "unit": "GB/s",
-                                    "ms": ps_ms, "host_s": ps_wall, "launches": n_str},
-            "plain_single_buffer_gbs": single_gbs,
-            "plain_over_batched": single_gbs / value * world,
-            "cpu_baseline": cpu,
-            "e2e": None,
-            "clocks": clocks,
-            "gpu_launches": launches,
-        }
-        print(json.dumps(line), flush=True)
-    plain.close()
+        one_by_one()
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        one_by_one()
+        e1.record(stream)
+        stream.synchronize()
+        out["per_string_launches"] = {"value": in_bytes / (e0.elapsed_time(e1) / 1e3) / 1e9,
+                                      "unit": "GB/s", "ms": e0.elapsed_time(e1),
+                                      "host_s": time.perf_counter() - t0, "launches": n_str}
+        plain.close()
+    out["_lay"], out["_is16"] = lay, is16
     ctx.close()
-    if world > 1:
-        dist.destroy_process_group()
+    return out
 
 
-SERVE_METRIC = ("sustained input GB/s and p50/p99 request latency, validated UTF-8<->UTF-16LE "
-                "transcoding through the serving loop (continuous batching)")
-
-
-def run_serving(args, rank, world, local):
-    """Serving workload: requests of log-uniform size over 64 B - 16 MiB
-    (windows of the per-profile corpora, profile uniform, direction 50/50),
-    1 % with one injected error, arriving as a Poisson process, replayed in
-    real time through the library's serving loop (dispatcher thread,
-    continuous batching, admission by bytes against a device pool). For each
-    arrival rate (a fraction of the plain kernel's GB/s measured in the same
-    run) it reports the sustained input GB/s and the p50/p99 latency from
-    arrival to completion."""
+def serving_section(gbu, torch, local, cases, d_corp, rates, seconds, plain_gbs, pool_bytes,
+                    slots, seed, min_requests=2000):
+    """The serving loop at each load in `rates` (fractions of `plain_gbs`):
+    Poisson arrivals of requests of log-uniform size over 64 B - 16 MiB
+    (windows of the resident corpora, profile uniform, direction 50/50), 1 %
+    with one injected error, replayed in real time through the library's
+    server. Returns the per-load sustained GB/s and p50/p99 latency."""
     from textgen import batch as tbatch
-    pool = textgen.process_pool()
-    import torch
-    import torch.distributed as dist
-
-    import paper_2212_05098_gb300 as gbu
-
-    torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl")
-    profiles = args.profiles.split(",")
-    cases = gen_inputs(profiles, args.size, rank, pool)
-    pool.shutdown()
     corpora = [(c["profile"], textgen.UTF8 if c["dir"] == "utf8_to_utf16le" else textgen.UTF16,
                 c["data"]) for c in cases]
-    gbu.load()
-    d_corp = [torch.from_numpy(c["data"]).cuda() for c in cases]
-
-    # the plain single-buffer kernel on the corpora: the reference rate
-    plain = gbu.Context(local)
-    plain.reserve(args.size)
-    scratch_out = torch.empty(2 * args.size + 64, dtype=torch.uint8, device="cuda")
-    res1 = torch.zeros(4, dtype=torch.int64, device="cuda")
-    stream = torch.cuda.Stream()
-    sh = stream.cuda_stream
-
-    def single():
-        for c, d in zip(cases, d_corp):
-            if c["dir"] == "utf8_to_utf16le":
-                gbu.gbu_utf8_to_utf16le_async(plain.handle, d.data_ptr(), d.numel(),
-                                              scratch_out.data_ptr(), d.numel(), res1.data_ptr(), sh)
-            else:
-                gbu.gbu_utf16le_to_utf8_async(plain.handle, d.data_ptr(), d.numel() // 2,
-                                              scratch_out.data_ptr(), 3 * (d.numel() // 2),
-                                              res1.data_ptr(), sh)
-
-    single()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(3):
-        single()
-    e1.record(stream)
-    stream.synchronize()
-    plain_gbs = 3 * sum(d.numel() for d in d_corp) / (e0.elapsed_time(e1) / 1e3) / 1e9
-    plain.close()
-    del scratch_out
-
-    srv = gbu.gbu_server_create(local, int(args.pool_gib * (1 << 30)), args.slots, 4096)
+    srv = gbu.gbu_server_create(local, int(pool_bytes), slots, 4096)
     if not srv:
         raise RuntimeError("server creation failed")
-    mean_bytes = (16 << 20) - 64
-    mean_bytes /= np.log((16 << 20) / 64)
+    mean_bytes = ((16 << 20) - 64) / np.log((16 << 20) / 64)
     sweep = []
-    sampler = ClockSampler(local)
-    t_wall0 = time.time()
-    launches0 = gbu.gbu_kernel_launch_count()
-    for ri, frac in enumerate(float(x) for x in args.rates.split(",")):
+    n0 = gbu.gbu_kernel_launch_count()
+    for ri, frac in enumerate(rates):
         rate = frac * plain_gbs * 1e9 / mean_bytes          # requests per second
-        n_req = int(min(200_000, max(2000, rate * args.serve_seconds)))
-        tr = tbatch.serving_trace(corpora, n_req, rate, seed=5 + 1000 * rank + ri)
+        n_req = int(min(200_000, max(min_requests, rate * seconds)))
+        tr = tbatch.serving_trace(corpora, n_req, rate, seed=seed + ri)
         lay = tr.layout
         keep, reqs = [], []
         for i in range(n_req):
@@ -895,32 +1001,192 @@ def run_serving(args, rank, world, local):
             "batches": len({comp[i].batch for i in range(n_req)}),
         })
         del keep
-    t_wall1 = time.time()
-    launches = gbu.gbu_kernel_launch_count() - launches0
-    sampler.stop()
-    clocks = sampler.summary(t_wall0, t_wall1)
     stats = gbu.gbu_server_stats(srv)
     gbu.gbu_server_destroy(srv)
     top = max(sweep, key=lambda x: x["sustained_gbs"])
+    return {"sweep": sweep, "sustained_gbs_best": top["sustained_gbs"],
+            "p50_ms_at_best": top["p50_ms"], "p99_ms_at_best": top["p99_ms"],
+            "plain_single_buffer_gbs": plain_gbs,
+            "plain_over_served": plain_gbs / top["sustained_gbs"],
+            "pool_bytes": stats.pool_bytes, "pool_high_water": stats.pool_high_water,
+            "slots": slots, "launches": gbu.gbu_kernel_launch_count() - n0}
+
+
+def plain_rate(gbu, torch, local, cases, d_corp, stream, size):
+    """Input GB/s of the plain single-buffer kernel on the corpora (3 passes)."""
+    plain = gbu.Context(local)
+    plain.reserve(size)
+    scratch_out = torch.empty(2 * size + 64, dtype=torch.uint8, device="cuda")
+    res1 = torch.zeros(4, dtype=torch.int64, device="cuda")
+    sh = stream.cuda_stream
+
+    def single():
+        for c, d in zip(cases, d_corp):
+            if c["dir"] == "utf8_to_utf16le":
+                gbu.gbu_utf8_to_utf16le_async(plain.handle, d.data_ptr(), d.numel(),
+                                              scratch_out.data_ptr(), d.numel(), res1.data_ptr(), sh)
+            else:
+                gbu.gbu_utf16le_to_utf8_async(plain.handle, d.data_ptr(), d.numel() // 2,
+                                              scratch_out.data_ptr(), 3 * (d.numel() // 2),
+                                              res1.data_ptr(), sh)
+
+    single()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(3):
+        single()
+    e1.record(stream)
+    stream.synchronize()
+    plain.close()
+    return 3 * sum(d.numel() for d in d_corp) / (e0.elapsed_time(e1) / 1e3) / 1e9
+
+
+def run_batched(args, rank, world, local):
+    """Batched workload: `--strings` independent strings, lengths log-uniform
+    over 16 B - 1 MiB (optionally scaled to `--batch-total` bytes), profile
+    uniform over the four, direction 50/50, each a window of that profile's
+    corpus (`--size` bytes per profile and encoding) cut at character
+    boundaries. One step = one launch of the autotuned batch (CUDA graph).
+    Also timed in the same run: the same strings as one plain-kernel launch
+    each, and the plain single-buffer kernel on the corpora themselves."""
+    pool = textgen.process_pool()
+    import torch
+    import torch.distributed as dist
+
+    import paper_2212_05098_gb300 as gbu
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    profiles = args.profiles.split(",")
+    cases = gen_inputs(profiles, args.size, rank, pool)
+    pool.shutdown()
+    gbu.load()
+    d_corp = [torch.from_numpy(c["data"]).cuda() for c in cases]
+    stream = torch.cuda.Stream()
+    single_gbs = plain_rate(gbu, torch, local, cases, d_corp, stream, args.size)
+    sampler = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    t_wall0 = time.time()
+    b = batched_section(gbu, torch, local, cases, d_corp, args.strings, 4 + 1000 * rank, stream,
+                        single_gbs, args.steps, args.warmup, world, args.batch_total)
+    t_wall1 = time.time()
+    sampler.stop()
+    clocks = sampler.summary(t_wall0, t_wall1)
+    peak, peak_src = measured_peak()
+    ms_launch = b["ms_per_launch"]
+    in_bytes, out_bytes = b["input_bytes"], b["output_bytes"]
+    roofline = {"kernel": KERNEL, "bound": "hbm",
+                "achieved": (in_bytes + out_bytes) / (ms_launch / 1e3) / 1e9, "peak": peak,
+                "unit": "GB/s", "frac": (in_bytes + out_bytes) / (ms_launch / 1e3) / 1e9 / peak,
+                "traffic": None, "peak_source": peak_src,
+                "algorithmic_bytes_per_launch": in_bytes + out_bytes, "avg_launch_ms": ms_launch}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        lay, is16 = b["_lay"], b["_is16"]
+        budget, done, t_c = args.cpu_sample, 0, 0.0
+        for i in range(lay.nbytes.size):
+            if done >= budget:
+                break
+            d = cases[int(lay.corpus[i])]["data"][int(lay.start[i]):int(lay.start[i] + lay.nbytes[i])]
+            t0 = time.perf_counter()
+            if is16[i]:
+                oracle.utf16le_to_utf8(d)
+            else:
+                oracle.utf8_to_utf16le(d)
+            t_c += time.perf_counter() - t0
+            done += d.size
+        cpu = {"value": done / t_c / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": f"oracle (scalar C, 1 thread) on the first strings of the batch, "
+                         f"{done / 1e9:.2f} GB, {t_c:.1f} s"}
     if rank == 0:
         line = {
-            "metric": SERVE_METRIC, "value": top["sustained_gbs"], "unit": "GB/s",
-            "n_gpus": world, "steps": len(sweep), "warmup": 0,
+            "metric": BATCH_METRIC, "value": b["value"], "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_launch,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u8+u16", "data": "synthetic (windows of seeded per-profile corpora)",
+            "config": {"workload": f"{b['strings']} strings, lengths log-uniform 16 B-1 MiB"
+                                   + (f" scaled to {args.batch_total} B total" if args.batch_total
+                                      else "")
+                                   + ", profiles uniform over 4, direction 50/50",
+                       "strings": b["strings"], "input_bytes": in_bytes,
+                       "output_bytes": out_bytes,
+                       "corpus_bytes_per_profile_and_encoding": args.size,
+                       "tune": b["tune"],
+                       "l2": "inputs read once per step from 8 corpora of "
+                             f"{args.size >> 20} MiB; no flush"},
+            "roofline": roofline,
+            "per_string_launches": b.get("per_string_launches"),
+            "plain_single_buffer_gbs": single_gbs,
+            "plain_over_batched": b["plain_over_batched"],
+            "cpu_baseline": cpu,
+            "e2e": None,
+            "clocks": clocks,
+            "gpu_launches": b["launches"],
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+SERVE_METRIC = ("sustained input GB/s and p50/p99 request latency, validated UTF-8<->UTF-16LE "
+                "transcoding through the serving loop (continuous batching)")
+
+
+def run_serving(args, rank, world, local):
+    """Serving workload: requests of log-uniform size over 64 B - 16 MiB
+    (windows of the per-profile corpora, profile uniform, direction 50/50),
+    1 % with one injected error, arriving as a Poisson process, replayed in
+    real time through the library's serving loop (dispatcher thread,
+    continuous batching, admission by bytes against a device pool). For each
+    arrival rate (a fraction of the plain kernel's GB/s measured in the same
+    run) it reports the sustained input GB/s and the p50/p99 latency from
+    arrival to completion."""
+    pool = textgen.process_pool()
+    import torch
+    import torch.distributed as dist
+
+    import paper_2212_05098_gb300 as gbu
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    profiles = args.profiles.split(",")
+    cases = gen_inputs(profiles, args.size, rank, pool)
+    pool.shutdown()
+    gbu.load()
+    d_corp = [torch.from_numpy(c["data"]).cuda() for c in cases]
+    stream = torch.cuda.Stream()
+    plain_gbs = plain_rate(gbu, torch, local, cases, d_corp, stream, args.size)
+    sampler = ClockSampler(local)
+    t_wall0 = time.time()
+    sv = serving_section(gbu, torch, local, cases, d_corp,
+                         [float(x) for x in args.rates.split(",")], args.serve_seconds,
+                         plain_gbs, args.pool_gib * (1 << 30), args.slots, 5 + 1000 * rank)
+    t_wall1 = time.time()
+    sampler.stop()
+    clocks = sampler.summary(t_wall0, t_wall1)
+    if rank == 0:
+        line = {
+            "metric": SERVE_METRIC, "value": sv["sustained_gbs_best"], "unit": "GB/s",
+            "n_gpus": world, "steps": len(sv["sweep"]), "warmup": 0,
             "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u8+u16",
             "data": "synthetic (windows of seeded per-profile corpora, 1 % injected errors)",
             "config": {"workload": "Poisson arrivals, sizes log-uniform 64 B-16 MiB, profiles "
                                    "uniform over 4, direction 50/50, 1 % injected errors",
-                       "pool_bytes": stats.pool_bytes, "pool_high_water": stats.pool_high_water,
+                       "pool_bytes": sv["pool_bytes"], "pool_high_water": sv["pool_high_water"],
                        "slots": args.slots, "max_batch_items": 4096,
                        "rates": "fractions of the plain kernel's GB/s in this run",
                        "latency": "scheduled arrival to completion observed by the dispatcher"},
-            "p50_ms_at_best": top["p50_ms"], "p99_ms_at_best": top["p99_ms"],
-            "sweep": sweep,
+            "p50_ms_at_best": sv["p50_ms_at_best"], "p99_ms_at_best": sv["p99_ms_at_best"],
+            "sweep": sv["sweep"],
             "plain_single_buffer_gbs": plain_gbs,
-            "plain_over_served": plain_gbs / top["sustained_gbs"],
+            "plain_over_served": sv["plain_over_served"],
             "cpu_baseline": None, "e2e": None, "clocks": clocks,
-            "gpu_launches": launches,
+            "gpu_launches": sv["launches"],
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -51,7 +51,7 @@ WORKLOAD = ("single 1 GiB buffer per text profile (latin, cyrillic, cjk, emoji),
             "(UTF-8->UTF-16LE, UTF-16LE->UTF-8), validated")
 DIRS = ("utf8_to_utf16le", "utf16le_to_utf8")
 KERNEL = "transcode_kernel"      # the one persistent kernel (both directions)
-KERNEL_SRC = {"transcode_kernel": "transcode.cu"}
+KERNEL_SRC = {"transcode_kernel": ("transcode.cuh", "transcode_256x48.cu")}
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -137,7 +137,7 @@ def measured_peak():
 def source_hash(kernel: str) -> str:
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2212_05098_gb300", "csrc")
-    for name in (KERNEL_SRC[kernel], "common.cuh", "kernels.h"):
+    for name in (*KERNEL_SRC[kernel], "common.cuh", "kernels.h"):
         with open(os.path.join(d, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -1194,13 +1194,17 @@ def run_serving(args, rank, world, local):
 
 
 LATENCY_METRIC = "latency of one validated transcoding call against input size (mix profile)"
+SPIN_CYCLES = 200_000   # ~0.1 ms of GPU clock ahead of every timed call
 
 
 def run_latency(args, rank, world, local):
     """Small-string regime (the paper's throughput against input length,
     Sec. 8): for input sizes 16 B .. 256 MiB of the mix profile, the median
-    device time of one asynchronous call (CUDA events) and the wall time of
-    one synchronous call (launch, wait, read the result), per direction."""
+    device time of one asynchronous call (CUDA events around the call, with
+    the stream held behind a short spin while the host enqueues them) and the
+    wall time of one synchronous call (launch, wait, read the result), per
+    direction; the device time also with the one-launch path off and on
+    every kernel shape pinned."""
     import torch
 
     import paper_2212_05098_gb300 as gbu
@@ -1211,6 +1215,21 @@ def run_latency(args, rank, world, local):
     gbu.load()
     ctx = gbu.Context(local)
     ctx.reserve(top)
+    # the same calls with the one-launch path off (every size on the persistent grid)
+    ctx_p = gbu.Context(local)
+    ctx_p.reserve(top)
+    if gbu.gbu_set_tune(ctx_p.handle, 1, 0, 0) != gbu.GBU_OK:
+        raise RuntimeError("set_tune failed")
+    # and on every kernel shape pinned (the default context picks one by size)
+    shapes = gbu.gbu_tune_shapes()
+    ctx_s = {}
+    for chunk, threads in shapes:
+        cs = gbu.Context(local)
+        cs.reserve(top)
+        if gbu.gbu_set_tune(cs.handle, 1, 0, gbu.GBU_SMALL_MAX_CHUNKS, chunk, threads) != gbu.GBU_OK:
+            raise RuntimeError("set_tune failed")
+        ctx_s[f"{chunk}x{threads}"] = cs
+    small_limit = gbu.GBU_SMALL_MAX_CHUNKS * 12288
     d8, d16 = torch.from_numpy(t8).cuda(), torch.from_numpy(t16).cuda()
     out = torch.empty(2 * top + 64, dtype=torch.uint8, device="cuda")
     res = torch.zeros(4, dtype=torch.int64, device="cuda")
@@ -1222,13 +1241,32 @@ def run_latency(args, rank, world, local):
         for direction, d in (("utf8_to_utf16le", d8), ("utf16le_to_utf8", d16)):
             n = size if direction == "utf8_to_utf16le" else size // 2
 
-            def call_async():
+            def call_async(c=ctx):
                 if direction == "utf8_to_utf16le":
-                    gbu.gbu_utf8_to_utf16le_async(ctx.handle, d.data_ptr(), n, out.data_ptr(), n,
+                    gbu.gbu_utf8_to_utf16le_async(c.handle, d.data_ptr(), n, out.data_ptr(), n,
                                                   res.data_ptr(), sh)
                 else:
-                    gbu.gbu_utf16le_to_utf8_async(ctx.handle, d.data_ptr(), n, out.data_ptr(),
+                    gbu.gbu_utf16le_to_utf8_async(c.handle, d.data_ptr(), n, out.data_ptr(),
                                                   3 * n, res.data_ptr(), sh)
+
+            def device_ms(c, reps):
+                for _ in range(3):
+                    call_async(c)
+                stream.synchronize()
+                dev = []
+                for _ in range(reps):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    # the stream waits behind a ~0.1 ms spin while the host
+                    # enqueues the events and the call, so that the events
+                    # time the GPU's work and not the host's launch overhead
+                    with torch.cuda.stream(stream):
+                        torch.cuda._sleep(SPIN_CYCLES)
+                    e0.record(stream)
+                    call_async(c)
+                    e1.record(stream)
+                    stream.synchronize()
+                    dev.append(e0.elapsed_time(e1))
+                return statistics.median(dev)
 
             def call_sync():
                 if direction == "utf8_to_utf16le":
@@ -1236,26 +1274,21 @@ def run_latency(args, rank, world, local):
                 return gbu.gbu_utf16le_to_utf8(ctx.handle, d.data_ptr(), n, out.data_ptr(), 3 * n, sh)
 
             reps = 20 if size <= (16 << 20) else 5
-            for _ in range(3):
-                call_async()
-            stream.synchronize()
-            dev = []
-            for _ in range(reps):
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                call_async()
-                e1.record(stream)
-                stream.synchronize()
-                dev.append(e0.elapsed_time(e1))
+            dev_ms = device_ms(ctx, reps)
+            pers_ms = device_ms(ctx_p, reps) if size <= small_limit else None
+            by_shape = {k: device_ms(cs, reps) * 1e3 for k, cs in ctx_s.items()}
             wall = []
             for _ in range(reps):
                 t0 = time.perf_counter()
                 r = call_sync()
                 wall.append(time.perf_counter() - t0)
-            dev_ms = statistics.median(dev)
             rows.append({"bytes": size, "direction": direction, "status": r.status,
+                         "path": "one-launch" if size <= small_limit else "persistent",
                          "device_us": dev_ms * 1e3, "sync_call_us": statistics.median(wall) * 1e6,
-                         "device_gbs": size / (dev_ms / 1e3) / 1e9})
+                         "device_gbs": size / (dev_ms / 1e3) / 1e9,
+                         "device_us_persistent": None if pers_ms is None else pers_ms * 1e3,
+                         "device_us_by_shape": by_shape,
+                         "best_shape": min(by_shape, key=by_shape.get)})
         size *= 4
     big = [r for r in rows if r["bytes"] == rows[-1]["bytes"]]
     if rank == 0:
@@ -1264,10 +1297,18 @@ def run_latency(args, rank, world, local):
                 "warmup": 3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
                 "dtype": "u8+u16", "data": "synthetic (mix profile, seed 0)",
                 "config": {"workload": "one call per size, 16 B to 256 MiB by factors of 4",
-                           "largest_gbs": {r["direction"]: r["device_gbs"] for r in big}},
+                           "largest_gbs": {r["direction"]: r["device_gbs"] for r in big},
+                           "one_launch_path_up_to_bytes": small_limit},
+                "device_us_4KiB": {r["direction"]: r["device_us"] for r in rows
+                                   if r["bytes"] == 4096},
+                "best_shape_by_size": {f"{r['bytes']}/{r['direction']}": r["best_shape"]
+                                       for r in rows},
                 "sizes": rows, "gpu_launches": None}
         print(json.dumps(line), flush=True)
     ctx.close()
+    ctx_p.close()
+    for cs in ctx_s.values():
+        cs.close()
 
 
 def _host_call(gbu, ctx, c, outs, sh):

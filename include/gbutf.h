@@ -248,17 +248,38 @@ int32_t gbu_batch_launch_graph(gbu_ctx *ctx, void *stream);
  * results never depend on them). look_width: status words each lane of the
  * look-back warp reads per round (1, 2, 4, 8 or 16; the 32 * look_width nearest
  * predecessors per round). ctas_per_sm: resident CTAs per SM of the
- * persistent grid (0: as many as fit, 1..that maximum otherwise). */
+ * persistent grid (0: as many as fit, 1..that maximum otherwise).
+ * small_chunks: a single-buffer call whose input spans at most this many
+ * chunks (counted from the 16-byte boundary at or before the input) runs as
+ * one thread-block cluster with one CTA per chunk instead of the persistent
+ * grid: no scratch, no counters, one launch (0: never; at most
+ * GBU_SMALL_MAX_CHUNKS). Batches always use the persistent grid.
+ * chunk_bytes, compute_threads: the kernel shape, one of those that
+ * gbu_tune_shapes lists (input bytes per chunk, i.e. UTF-8 bytes or twice
+ * the UTF-16 words, and compute threads per CTA); both 0: single-buffer calls
+ * pick the shape from the input's size and batches use the default shape
+ * (12288 bytes, 256 threads). A planned batch is counted again for a new
+ * shape at its next launch. */
+#define GBU_SMALL_MAX_CHUNKS 8
 typedef struct gbu_tune {
     int32_t look_width;
     int32_t ctas_per_sm;
+    int32_t small_chunks;
+    int32_t chunk_bytes;
+    int32_t compute_threads;
 } gbu_tune;
 
-/* Read / set the context's launch parameters (default {1, 0}). Setting them
+/* Read / set the context's launch parameters (default {1, 0, 8, 0, 0}). Setting them
  * drops the context's captured batch graph. GBU_INVALID_ARG for values
  * outside the ranges above. */
 int32_t gbu_get_tune(gbu_ctx *ctx, gbu_tune *tune);
 int32_t gbu_set_tune(gbu_ctx *ctx, const gbu_tune *tune);
+
+/* The compiled kernel shapes: writes up to `max_shapes` of them to `shapes`
+ * (chunk_bytes and compute_threads set; the other fields at their defaults)
+ * and returns how many there are (GBU_INVALID_ARG, a negative count, for bad
+ * arguments). The first is the default shape. */
+int32_t gbu_tune_shapes(gbu_tune *shapes, int32_t max_shapes);
 
 /* Bounded waits. Every wait inside the kernels (for a TMA copy, for a
  * predecessor chunk's prefix, for another warp of the CTA) gives up after
@@ -282,14 +303,16 @@ int32_t gbu_set_wait_limit(gbu_ctx *ctx, uint64_t ns);
 int32_t gbu_test_skip_chunks(gbu_ctx *ctx, uint32_t first_chunk);
 
 /* Autotune the planned batch: time one warm-up and three launches of it on
- * `stream` for every (look_width, ctas_per_sm) pair, keep the pair with the
- * lowest median time on the context and store it in *chosen (may be NULL).
- * The batch's outputs and results are written by every timed launch (the
- * same values each time). If `cache_path` is not NULL, a text file of lines
- * "<key> <look_width> <ctas_per_sm> <ms>" is consulted first (key: device
- * name, SM count, and the batch's item count and input bytes in powers of two
- * and UTF-16 / transcoding shares in tenths) and the new choice is appended
- * to it; a cached key skips the timing. Blocks until done. Returns GBU_OK,
+ * `stream` for every kernel shape (the batch counted again for each), every
+ * look_width and every ctas_per_sm the shape fits, keep the combination with
+ * the lowest median time on the context (small_chunks unchanged) and store it
+ * in *chosen (may be NULL). The batch's outputs and results are written by
+ * every timed launch (the same values each time). If `cache_path` is not
+ * NULL, a text file of lines "<key> <look_width> <ctas_per_sm> <chunk_bytes>
+ * <compute_threads> <ms>" is consulted first (key: device name, SM count, and
+ * the batch's item count and input bytes in powers of two and UTF-16 /
+ * transcoding shares in tenths) and the new choice is appended to it; a
+ * cached key skips the timing. Blocks until done. Returns GBU_OK,
  * GBU_INVALID_ARG or GBU_DEVICE_ERROR (a failing launch). */
 int32_t gbu_batch_autotune(gbu_ctx *ctx, void *stream, const char *cache_path, gbu_tune *chosen);
 
@@ -376,7 +399,9 @@ int32_t gbu_server_stats(gbu_server *srv, gbu_server_stats_t *stats);
  * calls share the array: calls that overlap on the GPU (other streams, other
  * host threads on the same device) race and must not be issued. Same
  * arguments, result and output rules as gbu_utf8_to_utf16le; calls no
- * cudaMalloc / cudaFree; waits for `stream`. */
+ * cudaMalloc / cudaFree; waits for `stream`. Inputs of at most
+ * GBU_SMALL_MAX_CHUNKS chunks take the one-launch path, which uses the array
+ * only for the result. */
 #define GBU_NOALLOC_MAX_BYTES (64ull << 20)
 gbu_result gbu_utf8_to_utf16le_noalloc(const uint8_t *d_in, uint64_t n_bytes,
                                        uint16_t *d_out, uint64_t cap_units, void *stream);

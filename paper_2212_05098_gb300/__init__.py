@@ -30,6 +30,7 @@ GBU_OUTPUT_TOO_SMALL = 16
 GBU_INVALID_ARG = 17
 GBU_DEVICE_ERROR = 18
 GBU_DEVICE_TIMEOUT = 19
+GBU_SMALL_MAX_CHUNKS = 8    # largest input (in 12 KiB chunks) of the one-launch path
 
 
 class gbu_result(ctypes.Structure):
@@ -67,7 +68,9 @@ class gbu_batch_item(ctypes.Structure):
 
 
 class gbu_tune(ctypes.Structure):
-    _fields_ = [("look_width", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
+    _fields_ = [("look_width", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("small_chunks", ctypes.c_int32), ("chunk_bytes", ctypes.c_int32),
+                ("compute_threads", ctypes.c_int32)]
 
 
 class gbu_request(ctypes.Structure):
@@ -126,6 +129,7 @@ SIGNATURES = {
     "gbu_batch_launch_graph": (_I32, [_VP, _VP]),
     "gbu_get_tune": (_I32, [_VP, ctypes.POINTER(gbu_tune)]),
     "gbu_set_tune": (_I32, [_VP, ctypes.POINTER(gbu_tune)]),
+    "gbu_tune_shapes": (_I32, [ctypes.POINTER(gbu_tune), ctypes.c_int32]),
     "gbu_set_wait_limit": (_I32, [_VP, _U64]),
     "gbu_test_skip_chunks": (_I32, [_VP, ctypes.c_uint32]),
     "gbu_batch_autotune": (_I32, [_VP, _VP, ctypes.c_char_p, ctypes.POINTER(gbu_tune)]),
@@ -318,9 +322,20 @@ def gbu_test_skip_chunks(ctx, first_chunk: int) -> int:
     return load().gbu_test_skip_chunks(ctx, first_chunk)
 
 
-def gbu_set_tune(ctx, look_width: int, ctas_per_sm: int) -> int:
-    t = gbu_tune(look_width, ctas_per_sm)
+def gbu_set_tune(ctx, look_width: int, ctas_per_sm: int,
+                 small_chunks: int = GBU_SMALL_MAX_CHUNKS, chunk_bytes: int = 0,
+                 compute_threads: int = 0) -> int:
+    t = gbu_tune(look_width, ctas_per_sm, small_chunks, chunk_bytes, compute_threads)
     return load().gbu_set_tune(ctx, ctypes.byref(t))
+
+
+def gbu_tune_shapes() -> list[tuple[int, int]]:
+    """The compiled kernel shapes as (chunk_bytes, compute_threads); the first
+    is the default."""
+    n = load().gbu_tune_shapes(None, 0)
+    arr = (gbu_tune * max(1, n))()
+    load().gbu_tune_shapes(arr, n)
+    return [(arr[i].chunk_bytes, arr[i].compute_threads) for i in range(n)]
 
 
 def gbu_batch_autotune(ctx, stream=0, cache_path: str | None = None):

@@ -1,8 +1,9 @@
 // C ABI of the library (declared in include/gbutf.h): contexts, scratch
 // management, the synchronous / asynchronous / host-buffer entry points, the
 // batch calls and their autotuner. Every step of the transcoding runs in the
-// kernel of transcode.cu; this file only validates arguments, sizes scratch,
-// enqueues work and times launches.
+// kernels of transcode.cuh (one translation unit per kernel shape) and
+// utf32.cu; this file only validates arguments, picks a kernel shape, sizes
+// scratch, enqueues work and times launches.
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -34,6 +35,42 @@ constexpr uint64_t kMaxUnits = 1ull << 39;
 namespace gbu {
 // Kernel launches of every entry point (gbu_kernel_launch_count).
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+const Variant &variant(int i)
+{
+    switch (i) {
+    case 1: return variant_256x32();
+    case 2: return variant_512x32();
+    case 3: return variant_128x48();
+    case 4: return variant_512x48();
+    default: return variant_256x48();
+    }
+}
+
+int variant_index(int threads, uint32_t chunk_bytes)
+{
+    for (int i = 0; i < kVariants; i++)
+        if (variant(i).threads == threads && variant(i).chunk_bytes == chunk_bytes) return i;
+    return -1;
+}
+
+__global__ void write_result_kernel(ResultSlot *dst, int32_t status, uint64_t in_offset,
+                                    uint64_t out_len)
+{
+    volatile ResultSlot *r = dst;
+    r->status = status;
+    r->reserved = 0;
+    r->in_offset = in_offset;
+    r->out_len = out_len;
+    __threadfence_system();
+}
+
+cudaError_t launch_write_result(ResultSlot *dst, int32_t status, uint64_t in_offset,
+                                uint64_t out_len, cudaStream_t stream)
+{
+    write_result_kernel<<<1, 1, 0, stream>>>(dst, status, in_offset, out_len);
+    return cudaGetLastError();
+}
 }  // namespace gbu
 
 namespace {
@@ -70,6 +107,9 @@ struct gbu_ctx {
     cudaStream_t capture_stream = nullptr;
     cudaGraphExec_t graph = nullptr;
     gbu::Tune tune;                   // launch parameters of every call on the context
+    std::vector<gbu_batch_item> batch_src;   // the planned batch as the caller gave it
+    gbu_result *batch_results = nullptr;
+    int batch_variant = 0;            // kernel shape the batch's chunks were counted for
     uint64_t wait_ns = 0;             // limit of the kernels' bounded waits (0: the default)
     uint32_t skip_chunks = 0;         // test hook: the next launch starts at this chunk
     // host-buffer pipeline: copy streams, per-slice events and mapped results
@@ -100,6 +140,31 @@ bool op_big_endian(int32_t op)
 {
     return op == GBU_OP_UTF8_TO_UTF16BE || op == GBU_OP_UTF16BE_TO_UTF8 ||
            op == GBU_OP_UTF8_LENGTH_FROM_UTF16BE;
+}
+
+// Kernel shape of a single-buffer call of `bytes` input bytes when the
+// context leaves the shape to the input's size (largest size of each class;
+// chosen from the latency sweep of every shape on GB300).
+struct SizeClass {
+    uint64_t max_bytes;
+    int variant;
+};
+constexpr SizeClass kSizeClasses[] = {{~0ull, 0}};
+
+int shape_for(const gbu_ctx *c, uint64_t bytes)
+{
+    if (c->tune.variant >= 0) return c->tune.variant;
+    for (const SizeClass &k : kSizeClasses)
+        if (bytes <= k.max_bytes) return k.variant;
+    return 0;
+}
+
+// Smallest chunk of any shape (scratch sized for it fits every shape).
+uint32_t min_chunk_bytes()
+{
+    uint32_t m = variant(0).chunk_bytes;
+    for (int i = 1; i < kVariants; i++) m = std::min(m, variant(i).chunk_bytes);
+    return m;
 }
 
 // Point a one-item job at the context's scratch.
@@ -169,11 +234,18 @@ int32_t enqueue(gbu_ctx *c, Op op, const void *in, uint64_t n, void *out, uint64
         return ok(launch_write_result(dst, GBU_OK, 0, 0, stream)) ? GBU_OK : GBU_DEVICE_ERROR;
     }
     const bool utf16 = utf16_in(op);
+    const Variant &V = variant(shape_for(c, utf16 ? 2 * n : n));
     Job J{};
-    J.item0 = make_item(in, n, utf16, out, cap, write, dst, 0, big_endian(op));
+    J.item0 = V.make_item(in, n, utf16, out, cap, write, dst, 0, big_endian(op));
     J.num_items = 1;
     J.total_chunks = J.item0.nchunks;
     J.validate = validate ? 1u : 0u;
+    if (J.total_chunks <= (uint32_t)c->tune.small_chunks && !c->skip_chunks) {
+        // a few chunks: one cluster launch, no scratch
+        const cudaError_t e = V.launch_small(J.item0, write, validate, stream);
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+        return ok(e) ? GBU_OK : GBU_DEVICE_ERROR;
+    }
     int32_t st = ensure_scratch(c, J.total_chunks, stream);
     if (st != GBU_OK) {
         c->dirty = true;
@@ -189,10 +261,10 @@ int32_t enqueue(gbu_ctx *c, Op op, const void *in, uint64_t n, void *out, uint64
             !ok(cudaStreamSynchronize(stream)))
             return GBU_DEVICE_ERROR;
     }
-    int grid = job_grid(c->device, c->tune);
+    int grid = V.grid(c->device, c->tune);
     if (grid <= 0) return GBU_DEVICE_ERROR;
     if ((uint32_t)grid > J.total_chunks) grid = (int)J.total_chunks;
-    const cudaError_t e = launch_job(J, write, grid, stream, c->tune.look, big_endian(op));
+    const cudaError_t e = V.launch_job(J, write, grid, stream, c->tune.look, big_endian(op));
     g_launches.fetch_add(1, std::memory_order_relaxed);
     if (!ok(e)) {
         c->dirty = true;
@@ -278,7 +350,8 @@ int32_t gbu_reserve(gbu_ctx *c, uint64_t max_input_bytes)
 {
     if (!c) return GBU_INVALID_ARG;
     if (!ok(cudaSetDevice(c->device))) return GBU_DEVICE_ERROR;
-    const uint64_t chunks = (max_input_bytes + 16 + kChunkBytes - 1) / kChunkBytes + 1;
+    const uint64_t cb = min_chunk_bytes();
+    const uint64_t chunks = (max_input_bytes + 16 + cb - 1) / cb + 1;
     int32_t st = ensure_scratch(c, chunks, nullptr);
     if (st == GBU_OK && !ok(cudaDeviceSynchronize())) st = GBU_DEVICE_ERROR;
     return st;
@@ -435,7 +508,7 @@ static gbu_result run_utf32_in(gbu_ctx *c, const uint32_t *d_in, uint64_t n, uin
     if (n == 0) return make(GBU_OK, 0, 0);
     if (!ok(cudaSetDevice(c->device))) return make(GBU_DEVICE_ERROR);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const uint64_t ntiles = (n + kTile32 - 1) / kTile32;
+    const uint64_t ntiles = utf32_tiles(d_in, n);
     if (!ensure_scratch32(c, utf32_scratch_bytes(ntiles), s)) return make(GBU_DEVICE_ERROR);
     if (!ok(launch_utf32_to_utf8(d_in, n, d_out, write ? cap : ~0ull, write, c->scratch32,
                                  reinterpret_cast<ResultSlot *>(c->d_result), s)))
@@ -454,7 +527,7 @@ static gbu_result run_utf8_to_32(gbu_ctx *c, const uint8_t *d_in, uint64_t n, ui
     if (v.status >= GBU_INVALID_ARG) return v;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const uint64_t p = v.status == GBU_OK ? n : v.in_offset;   // the valid prefix
-    const uint64_t ntiles = (p + kTile8 - 1) / kTile8;
+    const uint64_t ntiles = utf8_tiles(d_in, p);
     if (!ensure_scratch32(c, utf32_scratch_bytes(ntiles), s)) return make(GBU_DEVICE_ERROR);
     if (!ok(launch_utf8_to_utf32(d_in, n, p, v.status, v.in_offset, d_out, write ? cap : ~0ull,
                                  write, c->scratch32, reinterpret_cast<ResultSlot *>(c->d_result),
@@ -582,7 +655,8 @@ static gbu_result run_host(gbu_ctx *c, Op op, const void *h_in, uint64_t n, void
     // scratch for the largest slice, before anything is enqueued
     uint64_t max_units = 0;
     for (int k = 0; k < ns; k++) max_units = std::max(max_units, cuts[k + 1] - cuts[k]);
-    if (ensure_scratch(c, (16 + max_units * uin + kChunkBytes - 1) / kChunkBytes + 1, s) != GBU_OK)
+    const uint64_t cb = min_chunk_bytes();
+    if (ensure_scratch(c, (16 + max_units * uin + cb - 1) / cb + 1, s) != GBU_OK)
         return make(GBU_DEVICE_ERROR);
     if (!ok(cudaStreamSynchronize(s))) return make(GBU_DEVICE_ERROR);
     // Every return below first waits for all three streams: no copy may
@@ -690,33 +764,26 @@ static bool grow_batch(gbu_ctx *c, uint64_t items, uint64_t chunks)
     return true;
 }
 
-int32_t gbu_batch_plan(gbu_ctx *c, const gbu_batch_item *items, uint32_t count,
-                       gbu_result *results, void *stream)
+}  // extern "C"
+
+// Count the chunks of the context's batch for its kernel shape (the pinned
+// one, else the default), number them operation by operation, and copy the
+// descriptors to the device. The caller has validated the items.
+static int32_t plan_batch(gbu_ctx *c, cudaStream_t s)
 {
-    if (!c || (count && (!items || !results))) return GBU_INVALID_ARG;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (!ok(cudaSetDevice(c->device))) return GBU_DEVICE_ERROR;
-    // validate and count chunks
+    const gbu_batch_item *items = c->batch_src.data();
+    const uint32_t count = (uint32_t)c->batch_src.size();
+    const int vi = c->tune.variant >= 0 ? c->tune.variant : 0;
+    const Variant &V = variant(vi);
     uint64_t chunks = 0;
     bool any_write = false, any_be = false;
     for (uint32_t i = 0; i < count; i++) {
         const gbu_batch_item &b = items[i];
-        if (b.op < GBU_OP_UTF8_TO_UTF16LE || b.op > GBU_OP_UTF8_LENGTH_FROM_UTF16BE)
-            return GBU_INVALID_ARG;
-        const bool utf16 = op_utf16_in(b.op);
-        const bool write = op_writes(b.op);
-        if (b.n >= kMaxUnits || (b.n && !b.in)) return GBU_INVALID_ARG;
-        if (utf16 && (reinterpret_cast<uintptr_t>(b.in) & 1u)) return GBU_INVALID_ARG;
-        if (write && b.cap && !b.out) return GBU_INVALID_ARG;
-        if (write && !utf16 && (reinterpret_cast<uintptr_t>(b.out) & 1u)) return GBU_INVALID_ARG;
-        any_write |= write;
+        any_write |= op_writes(b.op);
         any_be |= op_big_endian(b.op);
-        const uint64_t units = utf16 ? kChunk16 : kChunk8;
-        const uint64_t head = b.n ? (utf16 ? ((reinterpret_cast<uintptr_t>(b.in) & 15u) >> 1)
-                                           : (reinterpret_cast<uintptr_t>(b.in) & 15u))
-                                  : 0;
-        chunks += b.n ? (head + b.n + units - 1) / units : 1;
+        chunks += chunks_of(V, b.in, b.n, op_utf16_in(b.op));
     }
+    c->batch_items = 0;
     if (chunks >= (1ull << 32)) return GBU_INVALID_ARG;
     if (!ok(cudaStreamSynchronize(s))) return GBU_DEVICE_ERROR;   // host staging is reused
     if (!grow_batch(c, count ? count : 1, chunks ? chunks : 1)) return GBU_DEVICE_ERROR;
@@ -728,9 +795,9 @@ int32_t gbu_batch_plan(gbu_ctx *c, const gbu_batch_item *items, uint32_t count,
         for (uint32_t i = 0; i < count; i++) {
             const gbu_batch_item &b = items[i];
             if (b.op != op) continue;
-            Item I = make_item(b.in, b.n, op_utf16_in(b.op), b.out, b.cap, op_writes(b.op),
-                               reinterpret_cast<ResultSlot *>(results + i), base,
-                               op_big_endian(b.op));
+            Item I = V.make_item(b.in, b.n, op_utf16_in(b.op), b.out, b.cap, op_writes(b.op),
+                                 reinterpret_cast<ResultSlot *>(c->batch_results + i), base,
+                                 op_big_endian(b.op));
             c->h_items[i] = I;
             for (uint32_t k = 0; k < I.nchunks; k++) c->h_chunk_item[base + k] = i;
             base += I.nchunks;
@@ -750,11 +817,44 @@ int32_t gbu_batch_plan(gbu_ctx *c, const gbu_batch_item *items, uint32_t count,
     c->batch_chunks = (uint32_t)chunks;
     c->batch_write = any_write;
     c->batch_be = any_be;
+    c->batch_variant = vi;
     if (c->graph) {
         cudaGraphExecDestroy(c->graph);
         c->graph = nullptr;
     }
     return GBU_OK;
+}
+
+// The planned batch counted for the context's current kernel shape.
+static int32_t plan_current(gbu_ctx *c, cudaStream_t s)
+{
+    const int vi = c->tune.variant >= 0 ? c->tune.variant : 0;
+    if (c->batch_src.empty() || c->batch_variant == vi) return GBU_OK;
+    return plan_batch(c, s);
+}
+
+extern "C" {
+
+int32_t gbu_batch_plan(gbu_ctx *c, const gbu_batch_item *items, uint32_t count,
+                       gbu_result *results, void *stream)
+{
+    if (!c || (count && (!items || !results))) return GBU_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!ok(cudaSetDevice(c->device))) return GBU_DEVICE_ERROR;
+    for (uint32_t i = 0; i < count; i++) {
+        const gbu_batch_item &b = items[i];
+        if (b.op < GBU_OP_UTF8_TO_UTF16LE || b.op > GBU_OP_UTF8_LENGTH_FROM_UTF16BE)
+            return GBU_INVALID_ARG;
+        const bool utf16 = op_utf16_in(b.op);
+        const bool write = op_writes(b.op);
+        if (b.n >= kMaxUnits || (b.n && !b.in)) return GBU_INVALID_ARG;
+        if (utf16 && (reinterpret_cast<uintptr_t>(b.in) & 1u)) return GBU_INVALID_ARG;
+        if (write && b.cap && !b.out) return GBU_INVALID_ARG;
+        if (write && !utf16 && (reinterpret_cast<uintptr_t>(b.out) & 1u)) return GBU_INVALID_ARG;
+    }
+    c->batch_src.assign(items, items + count);
+    c->batch_results = results;
+    return plan_batch(c, s);
 }
 
 // Enqueue the planned batch; `counted`: a real launch (not a graph capture).
@@ -770,10 +870,11 @@ static int32_t batch_enqueue(gbu_ctx *c, cudaStream_t s, bool counted = true)
     J.item_err = c->d_item_err;
     J.item_done = c->d_item_done;
     J.wait_ns = c->wait_ns;
-    int grid = job_grid(c->device, c->tune);
+    const Variant &V = variant(c->batch_variant);
+    int grid = V.grid(c->device, c->tune);
     if (grid <= 0) return GBU_DEVICE_ERROR;
     if ((uint32_t)grid > J.total_chunks) grid = (int)J.total_chunks;
-    const cudaError_t e = launch_job(J, c->batch_write, grid, s, c->tune.look, c->batch_be);
+    const cudaError_t e = V.launch_job(J, c->batch_write, grid, s, c->tune.look, c->batch_be);
     if (counted) g_launches.fetch_add(1, std::memory_order_relaxed);
     return ok(e) ? GBU_OK : GBU_DEVICE_ERROR;
 }
@@ -783,6 +884,7 @@ int32_t gbu_batch_launch(gbu_ctx *c, void *stream)
     if (!c) return GBU_INVALID_ARG;
     if (!ok(cudaSetDevice(c->device))) return GBU_DEVICE_ERROR;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (plan_current(c, s) != GBU_OK) return GBU_DEVICE_ERROR;
     if (c->dirty && ensure_scratch(c, c->batch_chunks ? c->batch_chunks : 1, s) != GBU_OK)
         return GBU_DEVICE_ERROR;
     return batch_enqueue(c, s);
@@ -793,13 +895,15 @@ int32_t gbu_batch_launch_graph(gbu_ctx *c, void *stream)
     if (!c) return GBU_INVALID_ARG;
     if (!ok(cudaSetDevice(c->device))) return GBU_DEVICE_ERROR;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (plan_current(c, s) != GBU_OK) return GBU_DEVICE_ERROR;
     if (c->batch_items == 0) return GBU_OK;
     if (c->dirty && ensure_scratch(c, c->batch_chunks, s) != GBU_OK) return GBU_DEVICE_ERROR;
     if (!c->graph) {
         if (!c->capture_stream &&
             !ok(cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking)))
             return GBU_DEVICE_ERROR;
-        if (job_max_grid(c->device) <= 0) return GBU_DEVICE_ERROR;   // attributes set before capture
+        // kernel attributes are set before the capture
+        if (variant(c->batch_variant).grid(c->device, Tune{}) <= 0) return GBU_DEVICE_ERROR;
         cudaGraph_t g = nullptr;
         if (!ok(cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal)))
             return GBU_DEVICE_ERROR;
@@ -844,6 +948,10 @@ int32_t gbu_get_tune(gbu_ctx *c, gbu_tune *t)
     if (!c || !t) return GBU_INVALID_ARG;
     t->look_width = c->tune.look;
     t->ctas_per_sm = c->tune.ctas_per_sm;
+    t->small_chunks = c->tune.small_chunks;
+    const bool pinned = c->tune.variant >= 0;
+    t->chunk_bytes = pinned ? (int32_t)variant(c->tune.variant).chunk_bytes : 0;
+    t->compute_threads = pinned ? variant(c->tune.variant).threads : 0;
     return GBU_OK;
 }
 
@@ -852,20 +960,51 @@ int32_t gbu_set_tune(gbu_ctx *c, const gbu_tune *t)
     if (!c || !t) return GBU_INVALID_ARG;
     bool known = false;
     for (const int w : kLookWidths) known |= w == t->look_width;
-    if (!known || t->ctas_per_sm < 0) return GBU_INVALID_ARG;
+    if (!known || t->ctas_per_sm < 0 || t->small_chunks < 0 || t->small_chunks > kSmallMaxChunks)
+        return GBU_INVALID_ARG;
+    int vi = -1;
+    if (t->chunk_bytes != 0 || t->compute_threads != 0) {
+        vi = variant_index(t->compute_threads, (uint32_t)t->chunk_bytes);
+        if (vi < 0) return GBU_INVALID_ARG;
+    }
     if (!ok(cudaSetDevice(c->device))) return GBU_DEVICE_ERROR;
-    const int per = job_max_ctas_per_sm(c->device);
-    if (per <= 0) return GBU_DEVICE_ERROR;
+    // CTAs per SM: at most what the pinned shape (every shape, when none is
+    // pinned) fits; shapes that fit fewer use as many as fit
+    int per = 0;
+    for (int i = 0; i < kVariants; i++) {
+        if (vi >= 0 && i != vi) continue;
+        const int p = variant(i).max_ctas_per_sm(c->device);
+        if (p <= 0) return GBU_DEVICE_ERROR;
+        per = std::max(per, p);
+    }
     if (t->ctas_per_sm > per) return GBU_INVALID_ARG;
-    if (c->tune.look != t->look_width || c->tune.ctas_per_sm != t->ctas_per_sm) {
+    c->tune.small_chunks = t->small_chunks;   // single-buffer calls only: no graph holds it
+    if (c->tune.look != t->look_width || c->tune.ctas_per_sm != t->ctas_per_sm ||
+        c->tune.variant != vi) {
         c->tune.look = t->look_width;
         c->tune.ctas_per_sm = t->ctas_per_sm;
+        c->tune.variant = vi;   // a planned batch is counted again at its next launch
         if (c->graph) {   // the captured launch has the old parameters
             cudaGraphExecDestroy(c->graph);
             c->graph = nullptr;
         }
     }
     return GBU_OK;
+}
+
+int32_t gbu_tune_shapes(gbu_tune *shapes, int32_t max_shapes)
+{
+    if (max_shapes < 0 || (max_shapes && !shapes)) return GBU_INVALID_ARG;
+    for (int i = 0; i < kVariants && i < max_shapes; i++) {
+        gbu_tune t{};
+        t.look_width = GBU_DEFAULT_LOOK;
+        t.ctas_per_sm = 0;
+        t.small_chunks = kSmallMaxChunks;
+        t.chunk_bytes = (int32_t)variant(i).chunk_bytes;
+        t.compute_threads = variant(i).threads;
+        shapes[i] = t;
+    }
+    return kVariants;
 }
 
 }  // extern "C"
@@ -904,13 +1043,17 @@ bool tune_lookup(const char *path, const std::string &key, gbu::Tune *t)
     FILE *f = std::fopen(path, "r");
     if (!f) return false;
     char line[512], k[400];
-    int look = 0, ctas = 0;
+    int look = 0, ctas = 0, chunk = 0, threads = 0;
     bool found = false;
     while (std::fgets(line, sizeof line, f)) {
         if (line[0] == '#') continue;
-        if (std::sscanf(line, "%399s %d %d", k, &look, &ctas) == 3 && key == k) {
+        if (std::sscanf(line, "%399s %d %d %d %d", k, &look, &ctas, &chunk, &threads) == 5 &&
+            key == k) {
+            const int vi = variant_index(threads, (uint32_t)chunk);
+            if (vi < 0) continue;
             t->look = look;   // the last entry for a key wins
             t->ctas_per_sm = ctas;
+            t->variant = vi;
             found = true;
         }
     }
@@ -928,67 +1071,79 @@ int32_t gbu_batch_autotune(gbu_ctx *c, void *stream, const char *cache_path, gbu
     if (!ok(cudaSetDevice(c->device))) return GBU_DEVICE_ERROR;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     auto report = [&]() {
-        if (chosen) {
-            chosen->look_width = c->tune.look;
-            chosen->ctas_per_sm = c->tune.ctas_per_sm;
-        }
+        if (chosen) gbu_get_tune(c, chosen);
         return GBU_OK;
     };
-    if (c->batch_items == 0) return report();
+    if (c->batch_src.empty()) return report();
+    if (plan_current(c, s) != GBU_OK) return GBU_DEVICE_ERROR;
     const std::string key = tune_key(c);
     if (key.empty()) return GBU_DEVICE_ERROR;
+    auto apply = [&](const gbu::Tune &b) {
+        const Variant &V = variant(b.variant);
+        gbu_tune t{b.look, b.ctas_per_sm, c->tune.small_chunks, (int32_t)V.chunk_bytes, V.threads};
+        int32_t st = gbu_set_tune(c, &t);
+        if (st == GBU_OK) st = plan_current(c, s);   // count the chunks for the shape now
+        return st;
+    };
     gbu::Tune cached;
-    if (cache_path && tune_lookup(cache_path, key, &cached)) {
-        gbu_tune t{cached.look, cached.ctas_per_sm};
-        if (gbu_set_tune(c, &t) == GBU_OK) return report();
-    }
-    const int per = job_max_ctas_per_sm(c->device);
-    if (per <= 0) return GBU_DEVICE_ERROR;
-    if (c->dirty && ensure_scratch(c, c->batch_chunks, s) != GBU_OK) return GBU_DEVICE_ERROR;
+    if (cache_path && tune_lookup(cache_path, key, &cached) && apply(cached) == GBU_OK)
+        return report();
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (!ok(cudaEventCreate(&e0)) || !ok(cudaEventCreate(&e1))) return GBU_DEVICE_ERROR;
+    const gbu::Tune saved = c->tune;
     gbu::Tune best = c->tune;
     float best_ms = 1e30f;
     int32_t st = GBU_OK;
     constexpr int kReps = 3;
-    for (const int look : kLookWidths) {
-        for (int ctas = 1; ctas <= per && st == GBU_OK; ctas++) {
-            c->tune.look = look;
-            c->tune.ctas_per_sm = ctas;
-            st = batch_enqueue(c, s);   // warm-up
-            std::vector<float> ms;
-            for (int r = 0; r < kReps && st == GBU_OK; r++) {
-                float t = 0;
-                if (!ok(cudaEventRecord(e0, s)) || (st = batch_enqueue(c, s)) != GBU_OK ||
-                    !ok(cudaEventRecord(e1, s)) || !ok(cudaEventSynchronize(e1)) ||
-                    !ok(cudaEventElapsedTime(&t, e0, e1))) {
-                    if (st == GBU_OK) st = GBU_DEVICE_ERROR;
-                    break;
+    // every shape (the batch counted again for each), look-back width and
+    // resident CTAs per SM
+    for (int vi = 0; vi < kVariants && st == GBU_OK; vi++) {
+        const int per = variant(vi).max_ctas_per_sm(c->device);
+        c->tune.variant = vi;
+        if (per <= 0 || (st = plan_current(c, s)) != GBU_OK ||
+            (c->dirty && ensure_scratch(c, c->batch_chunks, s) != GBU_OK)) {
+            if (st == GBU_OK) st = GBU_DEVICE_ERROR;
+            break;
+        }
+        for (const int look : kLookWidths) {
+            for (int ctas = 1; ctas <= per && st == GBU_OK; ctas++) {
+                c->tune.look = look;
+                c->tune.ctas_per_sm = ctas;
+                st = batch_enqueue(c, s);   // warm-up
+                std::vector<float> ms;
+                for (int r = 0; r < kReps && st == GBU_OK; r++) {
+                    float t = 0;
+                    if (!ok(cudaEventRecord(e0, s)) || (st = batch_enqueue(c, s)) != GBU_OK ||
+                        !ok(cudaEventRecord(e1, s)) || !ok(cudaEventSynchronize(e1)) ||
+                        !ok(cudaEventElapsedTime(&t, e0, e1))) {
+                        if (st == GBU_OK) st = GBU_DEVICE_ERROR;
+                        break;
+                    }
+                    ms.push_back(t);
                 }
-                ms.push_back(t);
-            }
-            if (st != GBU_OK) break;
-            std::sort(ms.begin(), ms.end());
-            if (ms[kReps / 2] < best_ms) {
-                best_ms = ms[kReps / 2];
-                best = c->tune;
+                if (st != GBU_OK) break;
+                std::sort(ms.begin(), ms.end());
+                if (ms[kReps / 2] < best_ms) {
+                    best_ms = ms[kReps / 2];
+                    best = c->tune;
+                }
             }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    c->tune = Tune{};
-    if (st != GBU_OK) return st;
-    gbu_tune t{best.look, best.ctas_per_sm};
-    st = gbu_set_tune(c, &t);
-    if (st != GBU_OK) return st;
-    if (c->graph) {
-        cudaGraphExecDestroy(c->graph);
-        c->graph = nullptr;
+    c->tune = saved;
+    if (st != GBU_OK) {
+        plan_current(c, s);
+        return st;
     }
+    st = apply(best);
+    if (st != GBU_OK) return st;
     if (cache_path) {
         if (FILE *f = std::fopen(cache_path, "a")) {
-            std::fprintf(f, "%s %d %d %.4f\n", key.c_str(), best.look, best.ctas_per_sm, best_ms);
+            const Variant &V = variant(best.variant);
+            std::fprintf(f, "%s %d %d %u %d %.4f\n", key.c_str(), best.look, best.ctas_per_sm,
+                         V.chunk_bytes, V.threads, best_ms);
             std::fclose(f);
         }
     }

@@ -7,7 +7,9 @@
 // plug-ins that are not allowed to own device memory at all. gbu_create /
 // gbu_reserve allocate scratch, so those callers get this entry point instead.
 //
-// It runs the same kernel as gbu_utf8_to_utf16le, but the kernel's scratch
+// It runs the same kernels as gbu_utf8_to_utf16le (the one-launch cluster
+// kernel for inputs of a few chunks, which needs no scratch, else the
+// persistent kernel), but the persistent kernel's scratch
 // (chunk counters, first-error word, look-back status words, per-chunk error
 // prefixes and the result slot) lives in one file-scope device array of fixed
 // size, which every GPU that loads this library holds until the process exits.
@@ -30,6 +32,8 @@ using namespace gbu;
 
 namespace {
 
+// The call runs the default kernel shape (256 compute threads x 48 bytes).
+static_assert(kChunkBytes == 256 * 48, "chunks of the default kernel shape");
 constexpr uint64_t kNoAllocChunks = (GBU_NOALLOC_MAX_BYTES + 15 + kChunkBytes - 1) / kChunkBytes;
 constexpr size_t kScratchBytes = kHeaderBytes + 16 * kNoAllocChunks;
 constexpr int kMaxDevices = 64;
@@ -79,11 +83,13 @@ extern "C" gbu_result gbu_utf8_to_utf16le_noalloc(const uint8_t *d_in, uint64_t 
     }
 
     Job J{};
-    J.item0 = make_item(d_in, n_bytes, false, d_out, cap_units, true, nullptr, 0);
+    const Variant &V = variant_256x48();
+    J.item0 = V.make_item(d_in, n_bytes, false, d_out, cap_units, true, nullptr, 0, false);
     J.num_items = 1;
     J.total_chunks = J.item0.nchunks;
     if (J.total_chunks > kNoAllocChunks) return fail(GBU_INVALID_ARG);
-    const int max_grid = job_max_grid(dev);
+    const bool small = J.total_chunks <= (uint32_t)kSmallMaxChunks;
+    const int max_grid = small ? 1 : V.grid(dev, Tune{});
     if (max_grid <= 0) return fail(GBU_DEVICE_ERROR);
 
     unsigned char *base;
@@ -97,6 +103,18 @@ extern "C" gbu_result gbu_utf8_to_utf16le_noalloc(const uint8_t *d_in, uint64_t 
             d.base = static_cast<unsigned char *>(p);
         }
         base = d.base;
+    }
+    gbu_result r;
+    if (small) {
+        // a few chunks: one cluster launch that touches nothing but the
+        // result slot
+        J.item0.result = reinterpret_cast<ResultSlot *>(base + kHdrResult);
+        if (V.launch_small(J.item0, true, false, s) != cudaSuccess) return fail(GBU_DEVICE_ERROR);
+        note_launch();
+        if (cudaMemcpyAsync(&r, base + kHdrResult, sizeof r, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return fail(GBU_DEVICE_ERROR);
+        return r;
     }
     // The array keeps whatever the previous call left: counters and flags must
     // start at zero and the first-error word at all ones.
@@ -118,9 +136,9 @@ extern "C" gbu_result gbu_utf8_to_utf16le_noalloc(const uint8_t *d_in, uint64_t 
     J.err_prefix = J.status + kNoAllocChunks;
     J.item0.result = reinterpret_cast<ResultSlot *>(base + kHdrResult);
     const int grid = (uint32_t)max_grid > J.total_chunks ? (int)J.total_chunks : max_grid;
-    if (launch_job(J, true, grid, s) != cudaSuccess) return fail(GBU_DEVICE_ERROR);
+    if (V.launch_job(J, true, grid, s, GBU_DEFAULT_LOOK, false) != cudaSuccess)
+        return fail(GBU_DEVICE_ERROR);
     note_launch();
-    gbu_result r;
     if (cudaMemcpyAsync(&r, base + kHdrResult, sizeof r, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
         return fail(GBU_DEVICE_ERROR);

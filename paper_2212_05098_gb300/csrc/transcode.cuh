@@ -32,9 +32,15 @@
 // its two words. Errors are located by the exact local rules described with
 // each chunk body; the minimum (position, kind) over a chunk and then over
 // the item is the sequential decoder's first error (the paper's ell).
+//
+// This file is the body of one kernel shape: a translation unit defines
+// GBU_THREADS (compute threads), GBU_BPT (input bytes per thread and chunk),
+// GBU_MIN_BLOCKS (resident CTAs per SM it is compiled for), GBU_VNS (its
+// namespace) and GBU_VARIANT_FN (the name of its descriptor) and includes it.
 #include "kernels.h"
 
 namespace gbu {
+namespace GBU_VNS {
 
 namespace {
 
@@ -882,21 +888,41 @@ struct ChunkRec {
     uint32_t end;                // producer / compute thread 0: no chunk here
 };
 
-// Producer lane: load global chunk c into stage `slot` and describe it in
-// `rec` (descriptor and item index fetched here). Returns false (and marks
-// the stage and the record as the end) when the job is exhausted.
-__device__ __forceinline__ bool produce(const Job &J, uint32_t c, int slot, uint8_t *stages,
+// A chunk to load: its global number, its item and the item's descriptor.
+struct Next {
+    uint32_t c, it;
+    Item I;
+};
+
+// Producer lane: the descriptor of global chunk c (two dependent global reads
+// in a batch, none for one item), fetched ahead of the load where possible.
+__device__ __forceinline__ Next describe(const Job &J, uint32_t c)
+{
+    Next n;
+    n.c = c;
+    n.it = 0;
+    if (c < J.total_chunks) {
+        n.it = J.chunk_item ? J.chunk_item[c] : 0u;
+        n.I = J.items ? J.items[n.it] : J.item0;
+    }
+    return n;
+}
+
+// Producer lane: load chunk n.c into stage `slot` and describe it in `rec`.
+// Returns false (and marks the stage and the record as the end) when the job
+// is exhausted.
+__device__ __forceinline__ bool produce(const Job &J, const Next &n, int slot, uint8_t *stages,
                                         Ring &R, ChunkRec &rec)
 {
     rec.err = ~0ull;
+    const uint32_t c = n.c, it = n.it;
     if (c >= J.total_chunks) {
         rec.end = 1;
         R.end[slot] = 1;
         mbar_arrive(&R.full[slot]);
         return false;
     }
-    const uint32_t it = J.chunk_item ? J.chunk_item[c] : 0u;
-    const Item I = J.items ? J.items[it] : J.item0;
+    const Item &I = n.I;
     rec.out = I.out;
     rec.cap = I.cap;
     rec.op = I.op;
@@ -976,8 +1002,8 @@ constexpr int kSlots = 16;
 static_assert(kSlots >= kStages + kDepth + kLbWarps + 2, "chunk records");
 
 // How chunks are dealt to CTAs: 0 round-robin (CTA b takes chunks b, b +
-// grid, ...); 1 claimed from a counter when a stage frees; 2 claimed from a
-// counter once the CTA's previous chunk is counted.
+// grid, ...); 1 claimed from a counter when a stage frees; 2 as 1, except
+// that transcoding claims a chunk once the CTA's previous chunk is counted.
 #ifndef GBU_CLAIM
 #define GBU_CLAIM 2
 #endif
@@ -1024,6 +1050,13 @@ transcode_kernel(const Job J)
         // ---- producer warp (lane 0): refill the ring, account for chunks ----
         if (tid != kThreads + 32 * kLbWarps) return;
         bool producing = true, ok = true;
+        // Transcoding claims a chunk just ahead of its processing, once the
+        // CTA's previous chunk is counted: the chunks of all CTAs are then
+        // processed about in the order of their numbers, so that look-backs
+        // rarely wait for a late predecessor. Validation and length-only
+        // calls (short per-chunk work, no offsets to wait for) claim a chunk
+        // as soon as a stage frees, its descriptor fetched ahead.
+        const bool late = kClaim == 2 && kWrite && !J.validate;
         // the next chunk of this CTA: round-robin (CTA b takes chunks b,
         // b + grid, ...) or claimed from the job's counter
         auto next_chunk = [&](uint32_t n) -> uint32_t {
@@ -1032,7 +1065,18 @@ transcode_kernel(const Job J)
         };
         uint32_t np = 0;   // chunks produced (the end marker included)
         for (int s = 0; s < kStages && producing; s++, np++)
-            producing = produce(J, next_chunk(np), s, stages, R, s_rec[np % kSlots]);
+            producing = produce(J, describe(J, next_chunk(np)), s, stages, R, s_rec[np % kSlots]);
+        Next nx{};
+        if (producing && !late) nx = describe(J, next_chunk(np));
+        // a multi-chunk item's done count comes back one step later (the
+        // atomic's round trip overlaps the next wait); its last chunk
+        // finishes the item's result
+        bool pend = false;
+        uint32_t pend_old = 0, pend_it = 0, pend_n = 0;
+        auto settle = [&]() {
+            if (pend && pend_old == pend_n - 1) finalize_item(J, pend_it, J.items[pend_it]);
+            pend = false;
+        };
         if (!producing)   // the other look-back warps stop at the next records
             for (int m = 1; m < kLbWarps; m++) s_rec[(np - 1 + m) % kSlots].end = 1;
         // chunk j's first error and offset are known once its stage is
@@ -1046,6 +1090,7 @@ transcode_kernel(const Job J)
                 ok = false;
                 break;
             }
+            settle();
             const ChunkRec &r = s_rec[j % kSlots];
             const uint64_t key = *reinterpret_cast<const volatile unsigned long long *>(&r.err);
             if (!J.items) {
@@ -1060,23 +1105,27 @@ transcode_kernel(const Job J)
                     J.err_prefix[r.chunk] = r.excl + (key & 0x7FFFu);
                     atomicMin(&J.item_err[r.itidx], ((key >> 23) << 8) | ((key >> 15) & 0xFFu));
                 }
-                if (atomic_add_acq_rel(&J.item_done[r.itidx], 1u) == r.nchunks - 1)
-                    finalize_item(J, r.itidx, J.items[r.itidx]);
+                pend_old = atomic_add_acq_rel(&J.item_done[r.itidx], 1u);
+                pend_it = r.itidx;
+                pend_n = r.nchunks;
+                pend = true;
             }
             if (producing) {
-                // kClaim 2: claim the chunk only once its predecessor in the
-                // CTA's sequence is counted, so that chunks are claimed just
-                // ahead of their processing
-                if (kClaim == 2 && !mbar_wait(&pend_bar[(np - 1) % kSlots], ((np - 1) / kSlots) & 1u, wlim)) {
-                    ok = false;
-                    break;
+                if (late) {
+                    if (!mbar_wait(&pend_bar[(np - 1) % kSlots], ((np - 1) / kSlots) & 1u, wlim)) {
+                        ok = false;
+                        break;
+                    }
+                    nx = describe(J, next_chunk(np));
                 }
-                producing = produce(J, next_chunk(np), (int)(j % kStages), stages, R, s_rec[np % kSlots]);
+                producing = produce(J, nx, (int)(j % kStages), stages, R, s_rec[np % kSlots]);
                 np++;
+                if (producing && !late) nx = describe(J, next_chunk(np));
                 if (!producing)
                     for (int m = 1; m < kLbWarps; m++) s_rec[(np - 1 + m) % kSlots].end = 1;
             }
         }
+        settle();
         if (!ok) atomicOr(J.flags, 1u);
         // the look-back warps are done (every inclusive prefix is out)
         if (!mbar_wait(&lb_exit, 0, wlim)) atomicOr(J.flags, 1u);
@@ -1328,6 +1377,164 @@ transcode_kernel(const Job J)
     }
 }
 
+// ===========================================================================
+// One-launch path for inputs of a few chunks
+//
+// An input of at most kSmallMaxChunks chunks is converted by one thread-block
+// cluster with one CTA per chunk and no persistent machinery: each CTA loads
+// its chunk (with the same 16 bytes of context on either side) by plain
+// 16-byte loads, runs the chunk body of the persistent kernel (phase 1, the
+// CTA scan, phase 2 into shared memory), and learns the output offset of its
+// chunk from the aggregates of the chunks before it, which every CTA writes
+// into the shared memory of every CTA of the cluster before the cluster
+// barrier. The first error and the result are gathered the same way in CTA 0.
+// Nothing is kept in global memory between launches (no status words,
+// counters or fences), and there is no wait other than the two hardware
+// cluster barriers.
+// ===========================================================================
+
+__device__ __forceinline__ void cluster_arrive_release()
+{
+    asm volatile("barrier.cluster.arrive.release;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait_acquire()
+{
+    asm volatile("barrier.cluster.wait.acquire;" ::: "memory");
+}
+// Store into the shared memory of CTA `rank` of the cluster, at the address
+// that `local` has in this CTA.
+__device__ __forceinline__ uint32_t cluster_addr(const void *local, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(local)), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void st_cluster_u32(const void *local, uint32_t rank, uint32_t v)
+{
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(cluster_addr(local, rank)), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_cluster_u64(const void *local, uint32_t rank, uint64_t v)
+{
+    asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(cluster_addr(local, rank)), "l"(v) : "memory");
+}
+
+constexpr size_t kSmallSmem = (size_t)kStageBytes + kOutBuf;
+
+// Grid = cluster = the item's chunks (1 .. kSmallMaxChunks); CTA k converts
+// chunk k. `validate`: the validation-only form (out_len reported as 0).
+template <bool kWrite, bool kBE>
+__global__ void __launch_bounds__(kThreads, 1) small_kernel(const Item I, uint32_t validate)
+{
+    extern __shared__ __align__(128) uint8_t dyn_smem[];
+    uint8_t *const stage = dyn_smem;
+    uint8_t *const obuf = dyn_smem + kStageBytes;
+    __shared__ uint32_t s_warp[kThreads / 32 + 1];
+    __shared__ uint32_t s_agg[kSmallMaxChunks];              // every chunk's output units
+    __shared__ unsigned long long s_key[kSmallMaxChunks];    // CTA 0: every chunk's first error
+    __shared__ unsigned long long s_err;
+
+    const uint32_t tid = threadIdx.x, k = blockIdx.x, nct = gridDim.x;
+    if (tid == 0) s_err = ~0ull;
+    const bool u16 = (I.op & kOpUtf16) != 0;
+    // the window of the persistent kernel's TMA load (16-byte aligned, whole
+    // 16-byte blocks)
+    {
+        const int64_t ub = u16 ? 2 : 1;
+        const int64_t v0b = (int64_t)k * kChunkBytes;
+        const int64_t endb = (((int64_t)I.head + (int64_t)I.n) * ub + 15) & ~(int64_t)15;
+        int64_t lo_b = v0b - (int64_t)kHalo;
+        if (lo_b < 0) lo_b = 0;
+        int64_t hi_b = v0b + (int64_t)(kChunkBytes + kHalo);
+        if (hi_b > endb) hi_b = endb;
+        uint8_t *dst = stage + (lo_b - (v0b - (int64_t)kHalo));
+        for (int64_t b = lo_b + 16 * (int64_t)tid; b < hi_b; b += 16 * kThreads)
+            *reinterpret_cast<uint4 *>(dst + (b - lo_b)) =
+                __ldg(reinterpret_cast<const uint4 *>(I.in_al + b));
+    }
+    __syncthreads();
+    const int64_t lo = I.head, hi = (int64_t)I.head + (int64_t)I.n;
+    bool interior;
+    int64_t vt;
+    uint32_t cnt;
+    St8 s8;
+    St16 s16;
+    if (u16) {
+        const int64_t v0 = (int64_t)k * kChunk16;
+        interior = v0 - 2 >= lo && v0 + (int64_t)kChunk16 + 2 <= hi;
+        vt = v0 + (int64_t)kU16 * tid;
+        cnt = chunk16_phase1<kBE>(s16, stage, interior, vt, lo, hi);
+    } else {
+        const int64_t v0 = (int64_t)k * kChunk8;
+        interior = v0 - 4 >= lo && v0 + (int64_t)kChunk8 + 4 <= hi;
+        vt = v0 + (int64_t)kBPT * tid;
+        cnt = chunk8_phase1(s8, stage, interior, vt, lo, hi);
+    }
+    uint32_t agg, nflag;
+    const uint32_t t_off = block_exclusive_scan_flag(cnt, false, s_warp, &agg, &nflag);
+    if (nct > 1) {
+        // the chunk's aggregate into every CTA of the cluster (the barrier
+        // completes while phase 2 runs)
+        if (tid == 0)
+            for (uint32_t r = 0; r < nct; r++) st_cluster_u32(&s_agg[k], r, agg);
+        cluster_arrive_release();
+    }
+    if (u16) {
+        chunk16_phase2<kWrite, kBE>(s16, stage, interior, obuf, t_off, 0, vt, lo, hi, &s_err);
+    } else {
+        uint16_t *pu = reinterpret_cast<uint16_t *>(obuf) + t_off;
+        chunk8_phase2<kWrite, kBE>(s8, stage, interior, pu, t_off, vt, lo, hi, &s_err);
+    }
+    uint64_t excl = 0, total = agg;
+    if (nct > 1) {
+        cluster_wait_acquire();
+        total = 0;
+        for (uint32_t r = 0; r < nct; r++) {
+            if (r == k) excl = total;
+            total += s_agg[r];
+        }
+    }
+    __syncthreads();   // the staged output and the chunk's first error are complete
+    if (kWrite && excl < I.cap) {
+        const uint32_t ub = u16 ? 1u : 2u;   // output unit bytes
+        uint64_t nw = agg;
+        if (nw > I.cap - excl) nw = I.cap - excl;
+        block_store_bytes(obuf, I.out + excl * ub, (uint32_t)(nw * ub));
+    }
+    uint64_t key = s_err;
+    uint64_t prefix = excl;   // output units before the chunk holding the first error
+    if (nct > 1) {
+        // every chunk's first error into CTA 0 (its output units counted
+        // from the chunk's start; CTA 0 adds the chunks before it)
+        if (tid == 0) st_cluster_u64(&s_key[k], 0, key);
+        cluster_arrive_release();
+        cluster_wait_acquire();
+        if (k != 0) return;
+        key = ~0ull;
+        uint64_t run = 0;
+        for (uint32_t r = 0; r < nct; r++) {
+            if (s_key[r] != ~0ull) {   // chunks hold increasing positions
+                key = s_key[r];
+                prefix = run;
+                break;
+            }
+            run += s_agg[r];
+        }
+    }
+    if (tid != 0) return;
+    const bool v = validate != 0;
+    if (key != ~0ull)
+        write_result(I, (int32_t)((key >> 15) & 0xFFu), key >> 23, prefix + (key & 0x7FFFu), v);
+    else
+        write_result(I, (kWrite && total > I.cap) ? kOutputTooSmall : kOk, I.n, total, v);
+}
+
+template <bool W>
+const void *small_fn(bool be)
+{
+    return be ? reinterpret_cast<const void *>(&small_kernel<W, true>)
+              : reinterpret_cast<const void *>(&small_kernel<W, false>);
+}
+
 int g_max_per_sm[64] = {0};
 int g_sms[64] = {0};
 
@@ -1372,6 +1579,12 @@ int job_max_ctas_per_sm(int device)
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)job_smem_bytes(w != 0)) != cudaSuccess)
                     return 0;
+    for (int be = 0; be < 2; be++)
+        if (cudaFuncSetAttribute(small_fn<true>(be != 0), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kSmallSmem) != cudaSuccess ||
+            cudaFuncSetAttribute(small_fn<false>(be != 0), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kSmallSmem) != cudaSuccess)
+            return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel_for(true, GBU_DEFAULT_LOOK, false), kBlock,
                                                       job_smem_bytes(true)) != cudaSuccess ||
         per < 1)
@@ -1389,11 +1602,6 @@ int job_grid(int device, const Tune &t)
     return g_sms[device] * use;
 }
 
-int job_max_grid(int device)
-{
-    return job_grid(device, Tune{});
-}
-
 cudaError_t launch_job(const Job &J, bool write, int grid, cudaStream_t stream, int look, bool be)
 {
     void *args[] = {const_cast<Job *>(&J)};
@@ -1401,22 +1609,32 @@ cudaError_t launch_job(const Job &J, bool write, int grid, cudaStream_t stream, 
                             job_smem_bytes(write), stream);
 }
 
-__global__ void write_result_kernel(ResultSlot *dst, int32_t status, uint64_t in_offset,
-                                    uint64_t out_len)
+cudaError_t launch_small(const Item &I, bool write, bool validate, cudaStream_t stream)
 {
-    volatile ResultSlot *r = dst;
-    r->status = status;
-    r->reserved = 0;
-    r->in_offset = in_offset;
-    r->out_len = out_len;
-    __threadfence_system();
-}
-
-cudaError_t launch_write_result(ResultSlot *dst, int32_t status, uint64_t in_offset,
-                                uint64_t out_len, cudaStream_t stream)
-{
-    write_result_kernel<<<1, 1, 0, stream>>>(dst, status, in_offset, out_len);
-    return cudaGetLastError();
+    const uint32_t nct = I.nchunks;
+    if (nct < 1 || nct > (uint32_t)kSmallMaxChunks) return cudaErrorInvalidValue;
+    if (kSmallSmem > 48 * 1024) {   // the attribute is set once per device
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || job_max_ctas_per_sm(dev) <= 0)
+            return cudaErrorInvalidValue;
+    }
+    const void *fn = write ? small_fn<true>((I.op & kOpBE) != 0) : small_fn<false>((I.op & kOpBE) != 0);
+    Item item = I;
+    uint32_t v = validate ? 1u : 0u;
+    void *args[] = {&item, &v};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nct);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = kSmallSmem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = nct;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = nct > 1 ? 1 : 0;
+    return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
 Item make_item(const void *in, uint64_t n, bool utf16, void *out, uint64_t cap, bool write,
@@ -1441,6 +1659,23 @@ Item make_item(const void *in, uint64_t n, bool utf16, void *out, uint64_t cap, 
     const uint64_t nch = n ? (I.head + n + units - 1) / units : 1;
     I.nchunks = (uint32_t)nch;
     return I;
+}
+
+}  // namespace GBU_VNS
+
+const Variant &GBU_VARIANT_FN()
+{
+    static const Variant v = {kThreads,
+                              kBPT,
+                              kMinBlocks,
+                              kChunkBytes,
+                              &GBU_VNS::make_item,
+                              &GBU_VNS::job_smem_bytes,
+                              &GBU_VNS::job_max_ctas_per_sm,
+                              &GBU_VNS::job_grid,
+                              &GBU_VNS::launch_job,
+                              &GBU_VNS::launch_small};
+    return v;
 }
 
 }  // namespace gbu

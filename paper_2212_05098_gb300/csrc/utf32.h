@@ -11,6 +11,9 @@ namespace gbu {
 // of kThreads each; scratch of utf32_scratch_bytes(tiles) bytes, 16-aligned.
 constexpr uint32_t kTile32 = 8 * kThreads;
 constexpr uint32_t kTile8 = 32 * kThreads;
+// Tiles of a call: counted from the 16-byte boundary at or before the input.
+uint64_t utf32_tiles(const uint32_t *in, uint64_t n);
+uint64_t utf8_tiles(const uint8_t *in, uint64_t p);
 size_t utf32_scratch_bytes(uint64_t ntiles);
 // UTF-32LE -> UTF-8 (write = false: length / validation only); the result
 // lands in *res at stream completion.

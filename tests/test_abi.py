@@ -47,3 +47,11 @@ def test_null_context_is_invalid_argument():
     # argument checks happen before any CUDA call
     r = gbu.gbu_utf8_to_utf16le(None, None, 0, None, 0, None)
     assert r.status == gbu.GBU_INVALID_ARG
+
+
+def test_kernel_shapes_without_gpu():
+    shapes = gbu.gbu_tune_shapes()
+    assert shapes[0] == (12288, 256)            # the default shape first
+    assert len(set(shapes)) == len(shapes) >= 2
+    for chunk, threads in shapes:
+        assert chunk % threads == 0 and (chunk // threads) % 16 == 0

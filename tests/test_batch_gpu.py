@@ -219,10 +219,18 @@ def test_batch_invalid_items(ctx):
     assert gbu.gbu_batch_plan(ctx, [(p, 4, p, 4, 0)], 0, 0) == gbu.GBU_INVALID_ARG
 
 
+SHAPES = [(12288, 256), (8192, 256), (16384, 512), (6144, 128), (24576, 512)]
+
+
+def test_compiled_shapes():
+    assert gbu.gbu_tune_shapes() == SHAPES
+
+
+@pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("look", [1, 2, 4, 8, 16])
-def test_results_do_not_depend_on_tuning(ctx, look):
-    """Every (look-back width, CTAs per SM) gives the oracle's results, for a
-    batch and for single-buffer calls."""
+def test_results_do_not_depend_on_tuning(ctx, look, shape):
+    """Every kernel shape, look-back width and CTAs per SM gives the oracle's
+    results, for a batch and for single-buffer calls."""
     import torch
     from gpu_util import check_u16, check_u8
     rng = np.random.default_rng(81)
@@ -233,12 +241,12 @@ def test_results_do_not_depend_on_tuning(ctx, look):
     bad8 = textgen.mutate(t8.data, 2, seed=84)
     try:
         for ctas in (1, 2, 3):
-            st = gbu.gbu_set_tune(ctx, look, ctas)
+            st = gbu.gbu_set_tune(ctx, look, ctas, gbu.GBU_SMALL_MAX_CHUNKS, *shape)
             if ctas > 1 and st == gbu.GBU_INVALID_ARG:
                 break   # more CTAs per SM than fit on this device
             assert st == gbu.GBU_OK
             t = gbu.gbu_get_tune(ctx)
-            assert (t.look_width, t.ctas_per_sm) == (look, ctas)
+            assert (t.look_width, t.ctas_per_sm, t.chunk_bytes, t.compute_threads) == (look, ctas, *shape)
             assert gbu.gbu_batch_plan(ctx, b.items, b.res.data_ptr(), 0) == gbu.GBU_OK
             _run(ctx, b, gbu.gbu_batch_launch, times=1)
             _run(ctx, b, gbu.gbu_batch_launch_graph, times=1)
@@ -254,8 +262,11 @@ def test_tune_rejects_bad_values(ctx):
     assert gbu.gbu_set_tune(ctx, 5, 0) == gbu.GBU_INVALID_ARG
     assert gbu.gbu_set_tune(ctx, 8, -1) == gbu.GBU_INVALID_ARG
     assert gbu.gbu_set_tune(ctx, 8, 1000) == gbu.GBU_INVALID_ARG
+    assert gbu.gbu_set_tune(ctx, 8, 0, 8, 12288, 128) == gbu.GBU_INVALID_ARG   # not compiled
+    assert gbu.gbu_set_tune(ctx, 8, 0, 8, 4096, 0) == gbu.GBU_INVALID_ARG
+    assert gbu.gbu_set_tune(ctx, 8, 2, 8, 16384, 512) == gbu.GBU_INVALID_ARG   # fits one per SM
     t = gbu.gbu_get_tune(ctx)
-    assert (t.look_width, t.ctas_per_sm) == (1, 0)
+    assert (t.look_width, t.ctas_per_sm, t.chunk_bytes, t.compute_threads) == (1, 0, 0, 0)
 
 
 def test_autotune_and_cache(ctx, tmp_path):
@@ -267,12 +278,16 @@ def test_autotune_and_cache(ctx, tmp_path):
     try:
         st, t = gbu.gbu_batch_autotune(ctx, 0, cache)
         assert st == gbu.GBU_OK and t.look_width in (1, 2, 4, 8, 16) and 1 <= t.ctas_per_sm <= 3
+        assert (t.chunk_bytes, t.compute_threads) in SHAPES
+        chosen = [str(x) for x in (t.look_width, t.ctas_per_sm, t.chunk_bytes, t.compute_threads)]
         lines = [l for l in open(cache) if l.strip()]
-        assert len(lines) == 1 and lines[0].split()[1:3] == [str(t.look_width), str(t.ctas_per_sm)]
+        assert len(lines) == 1 and lines[0].split()[1:5] == chosen
+        _run(ctx, b, gbu.gbu_batch_launch_graph)    # on the chosen shape
         # a cached key is taken without timing and without a new line
         assert gbu.gbu_set_tune(ctx, 1, 0) == gbu.GBU_OK
         st2, t2 = gbu.gbu_batch_autotune(ctx, 0, cache)
-        assert st2 == gbu.GBU_OK and (t2.look_width, t2.ctas_per_sm) == (t.look_width, t.ctas_per_sm)
+        assert st2 == gbu.GBU_OK
+        assert [str(x) for x in (t2.look_width, t2.ctas_per_sm, t2.chunk_bytes, t2.compute_threads)] == chosen
         assert len([l for l in open(cache) if l.strip()]) == 1
         _run(ctx, b, gbu.gbu_batch_launch_graph)
     finally:

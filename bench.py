@@ -628,6 +628,8 @@ def main():
             "roofline": roofline,
             "directions": directions,
             "per_buffer_input_gbs": per_case,
+            "per_buffer_output_bytes": {f"{c['profile']}/{c['dir']}":
+                                        c["alg_bytes"] - c["data"].size for c in cases},
             "validate_only_input_gbs": validate_gbs,
             **extras,
             "cpu_baseline": cpu,
@@ -903,6 +905,7 @@ def batched_section(gbu, torch, local, cases, d_corp, n_strings, seed, stream, p
            "p50_launch_ms": float(np.percentile(ms_list, 50)),
            "p99_launch_ms": float(np.percentile(ms_list, 99)),
            "tune": {"look_width": tune.look_width, "ctas_per_sm": tune.ctas_per_sm,
+                    "chunk_bytes": tune.chunk_bytes, "compute_threads": tune.compute_threads,
                     "autotune_s": round(t_tune, 3)},
            "plain_single_buffer_gbs": plain_gbs,
            "plain_over_batched": plain_gbs / (value / world),
@@ -1229,13 +1232,36 @@ def run_latency(args, rank, world, local):
         if gbu.gbu_set_tune(cs.handle, 1, 0, gbu.GBU_SMALL_MAX_CHUNKS, chunk, threads) != gbu.GBU_OK:
             raise RuntimeError("set_tune failed")
         ctx_s[f"{chunk}x{threads}"] = cs
-    small_limit = gbu.GBU_SMALL_MAX_CHUNKS * 12288
+    small_limit = gbu.GBU_SMALL_MAX_CHUNKS * max(c for c, _ in shapes)
     d8, d16 = torch.from_numpy(t8).cuda(), torch.from_numpy(t16).cuda()
     out = torch.empty(2 * top + 64, dtype=torch.uint8, device="cuda")
     res = torch.zeros(4, dtype=torch.int64, device="cuda")
     stream = torch.cuda.Stream()
     sh = stream.cuda_stream
     rows = []
+    # floors of the same measurement: an empty launch (torch's spin kernel for
+    # one cycle), and a call on an empty input (one 1-thread kernel that
+    # writes the result with a system-scope fence)
+    def floor_us(launch):
+        ts = []
+        for _ in range(20):
+            with torch.cuda.stream(stream):
+                torch.cuda._sleep(SPIN_CYCLES)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            launch()
+            e1.record(stream)
+            stream.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts) * 1e3
+
+    def empty_kernel():
+        with torch.cuda.stream(stream):
+            torch.cuda._sleep(1)
+
+    empty_launch_us = floor_us(empty_kernel)
+    empty_call_us = floor_us(
+        lambda: gbu.gbu_utf8_to_utf16le_async(ctx.handle, 0, 0, 0, 0, res.data_ptr(), sh))
     size = 16
     while size <= top:
         for direction, d in (("utf8_to_utf16le", d8), ("utf16le_to_utf8", d16)):
@@ -1274,6 +1300,9 @@ def run_latency(args, rank, world, local):
                 return gbu.gbu_utf16le_to_utf8(ctx.handle, d.data_ptr(), n, out.data_ptr(), 3 * n, sh)
 
             reps = 20 if size <= (16 << 20) else 5
+            shp = gbu.gbu_call_shape(ctx.handle, size)
+            path = ("one-launch" if size <= shp.small_chunks * shp.chunk_bytes   # aligned input
+                    else "persistent")
             dev_ms = device_ms(ctx, reps)
             pers_ms = device_ms(ctx_p, reps) if size <= small_limit else None
             by_shape = {k: device_ms(cs, reps) * 1e3 for k, cs in ctx_s.items()}
@@ -1283,7 +1312,8 @@ def run_latency(args, rank, world, local):
                 r = call_sync()
                 wall.append(time.perf_counter() - t0)
             rows.append({"bytes": size, "direction": direction, "status": r.status,
-                         "path": "one-launch" if size <= small_limit else "persistent",
+                         "path": path,
+                         "shape": f"{shp.chunk_bytes}x{shp.compute_threads}",
                          "device_us": dev_ms * 1e3, "sync_call_us": statistics.median(wall) * 1e6,
                          "device_gbs": size / (dev_ms / 1e3) / 1e9,
                          "device_us_persistent": None if pers_ms is None else pers_ms * 1e3,
@@ -1298,9 +1328,11 @@ def run_latency(args, rank, world, local):
                 "dtype": "u8+u16", "data": "synthetic (mix profile, seed 0)",
                 "config": {"workload": "one call per size, 16 B to 256 MiB by factors of 4",
                            "largest_gbs": {r["direction"]: r["device_gbs"] for r in big},
-                           "one_launch_path_up_to_bytes": small_limit},
+                           "one_launch_path": "inputs of at most 8 chunks of the call's shape"},
                 "device_us_4KiB": {r["direction"]: r["device_us"] for r in rows
                                    if r["bytes"] == 4096},
+                "device_us_empty_launch": empty_launch_us,
+                "device_us_empty_call": empty_call_us,
                 "best_shape_by_size": {f"{r['bytes']}/{r['direction']}": r["best_shape"]
                                        for r in rows},
                 "sizes": rows, "gpu_launches": None}

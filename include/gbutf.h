@@ -281,6 +281,14 @@ int32_t gbu_set_tune(gbu_ctx *ctx, const gbu_tune *tune);
  * arguments). The first is the default shape. */
 int32_t gbu_tune_shapes(gbu_tune *shapes, int32_t max_shapes);
 
+/* The launch parameters a single-buffer call on `ctx` with `input_bytes`
+ * bytes of input uses (the kernel shape filled in even when the context
+ * picks it by size: up to 1 MiB 8192 x 256, above 12288 x 256). Such a call
+ * runs as one cluster launch when its input spans at most small_chunks
+ * chunks of chunk_bytes (counted from the 16-byte boundary at or before it).
+ * Returns GBU_OK or GBU_INVALID_ARG. */
+int32_t gbu_call_shape(gbu_ctx *ctx, uint64_t input_bytes, gbu_tune *tune);
+
 /* Bounded waits. Every wait inside the kernels (for a TMA copy, for a
  * predecessor chunk's prefix, for another warp of the CTA) gives up after
  * `ns` nanoseconds of GPU global time (0 restores the default, 1 s). A wait

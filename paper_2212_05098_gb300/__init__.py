@@ -130,6 +130,7 @@ SIGNATURES = {
     "gbu_get_tune": (_I32, [_VP, ctypes.POINTER(gbu_tune)]),
     "gbu_set_tune": (_I32, [_VP, ctypes.POINTER(gbu_tune)]),
     "gbu_tune_shapes": (_I32, [ctypes.POINTER(gbu_tune), ctypes.c_int32]),
+    "gbu_call_shape": (_I32, [_VP, _U64, ctypes.POINTER(gbu_tune)]),
     "gbu_set_wait_limit": (_I32, [_VP, _U64]),
     "gbu_test_skip_chunks": (_I32, [_VP, ctypes.c_uint32]),
     "gbu_batch_autotune": (_I32, [_VP, _VP, ctypes.c_char_p, ctypes.POINTER(gbu_tune)]),
@@ -327,6 +328,15 @@ def gbu_set_tune(ctx, look_width: int, ctas_per_sm: int,
                  compute_threads: int = 0) -> int:
     t = gbu_tune(look_width, ctas_per_sm, small_chunks, chunk_bytes, compute_threads)
     return load().gbu_set_tune(ctx, ctypes.byref(t))
+
+
+def gbu_call_shape(ctx, input_bytes: int) -> gbu_tune:
+    """Launch parameters of a single-buffer call with this many input bytes."""
+    t = gbu_tune()
+    st = load().gbu_call_shape(ctx, input_bytes, ctypes.byref(t))
+    if st != GBU_OK:
+        raise RuntimeError(status_name(st))
+    return t
 
 
 def gbu_tune_shapes() -> list[tuple[int, int]]:

@@ -16,6 +16,7 @@
 #include "../../include/gbutf.h"
 #include "kernels.h"
 #include "utf32.h"
+#include "validate.h"
 
 using namespace gbu;
 
@@ -143,13 +144,17 @@ bool op_big_endian(int32_t op)
 }
 
 // Kernel shape of a single-buffer call of `bytes` input bytes when the
-// context leaves the shape to the input's size (largest size of each class;
-// chosen from the latency sweep of every shape on GB300).
+// context leaves the shape to the input's size (largest size of each class).
+// From the latency sweep of every shape on GB300 (device time per call, both
+// directions, mix profile): up to 1 MiB the 8 KiB chunks of 256 x 32 are
+// fastest (the 12 KiB shape is 2-4 us slower per call: longer per-thread
+// work and code path); from 16 MiB the default 256 x 48 is (4 MiB: within
+// the timer's 2 us steps).
 struct SizeClass {
     uint64_t max_bytes;
     int variant;
 };
-constexpr SizeClass kSizeClasses[] = {{~0ull, 0}};
+constexpr SizeClass kSizeClasses[] = {{1ull << 20, 1}, {~0ull, 0}};
 
 int shape_for(const gbu_ctx *c, uint64_t bytes)
 {
@@ -204,9 +209,10 @@ int32_t ensure_scratch(gbu_ctx *c, uint64_t chunks, cudaStream_t stream)
         c->dirty = true;
     }
     if (c->dirty) {
-        // chunks_done = exit = flags = done = 0, first-error word = ~0, epoch = 0,
-        // and no status word may look ready
-        static const uint64_t hdr[4] = {0, 0, ~0ull, 0};
+        // chunks_done = exit = flags = done = 0, first-error word = ~0, epoch =
+        // claim = 0, the validation kernel's first-error word = ~0, and no
+        // status word may look ready
+        static const uint64_t hdr[5] = {0, 0, ~0ull, 0, ~0ull};
         if (!ok(cudaMemcpyAsync(c->scratch, hdr, sizeof hdr, cudaMemcpyHostToDevice, stream)) ||
             !ok(cudaMemsetAsync(c->scratch + kHeaderBytes, 0, 8 * c->max_chunks, stream)))
             return GBU_DEVICE_ERROR;
@@ -246,10 +252,21 @@ int32_t enqueue(gbu_ctx *c, Op op, const void *in, uint64_t n, void *out, uint64
         g_launches.fetch_add(1, std::memory_order_relaxed);
         return ok(e) ? GBU_OK : GBU_DEVICE_ERROR;
     }
-    int32_t st = ensure_scratch(c, J.total_chunks, stream);
+    int32_t st = ensure_scratch(c, validate && !c->skip_chunks ? 1 : J.total_chunks, stream);
     if (st != GBU_OK) {
         c->dirty = true;
         return st;
+    }
+    if (validate && !c->skip_chunks) {
+        // a validation needs no offsets: the streaming kernel (two launches)
+        unsigned long long *err = reinterpret_cast<unsigned long long *>(c->scratch + kHdrValidErr);
+        const cudaError_t e = launch_validate(in, n, utf16, big_endian(op), err, dst, stream);
+        g_launches.fetch_add(2, std::memory_order_relaxed);
+        if (!ok(e)) {
+            c->dirty = true;
+            return GBU_DEVICE_ERROR;
+        }
+        return GBU_OK;
     }
     attach_scratch(c, J);
     J.wait_ns = c->wait_ns;
@@ -784,7 +801,7 @@ static int32_t plan_batch(gbu_ctx *c, cudaStream_t s)
         chunks += chunks_of(V, b.in, b.n, op_utf16_in(b.op));
     }
     c->batch_items = 0;
-    if (chunks >= (1ull << 32)) return GBU_INVALID_ARG;
+    if (chunks >= (1ull << 31)) return GBU_INVALID_ARG;   // the claim counter may run past the end
     if (!ok(cudaStreamSynchronize(s))) return GBU_DEVICE_ERROR;   // host staging is reused
     if (!grow_batch(c, count ? count : 1, chunks ? chunks : 1)) return GBU_DEVICE_ERROR;
     // Chunks are numbered operation by operation (items keep their index and
@@ -989,6 +1006,18 @@ int32_t gbu_set_tune(gbu_ctx *c, const gbu_tune *t)
             c->graph = nullptr;
         }
     }
+    return GBU_OK;
+}
+
+int32_t gbu_call_shape(gbu_ctx *c, uint64_t input_bytes, gbu_tune *t)
+{
+    if (!c || !t) return GBU_INVALID_ARG;
+    const int vi = shape_for(c, input_bytes);
+    t->look_width = c->tune.look;
+    t->ctas_per_sm = c->tune.ctas_per_sm;
+    t->small_chunks = c->tune.small_chunks;
+    t->chunk_bytes = (int32_t)variant(vi).chunk_bytes;
+    t->compute_threads = variant(vi).threads;
     return GBU_OK;
 }
 

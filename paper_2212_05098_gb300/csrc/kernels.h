@@ -17,7 +17,7 @@ constexpr int kMinBlocks = GBU_MIN_BLOCKS;
 
 // Scratch header shared by every job launch on one scratch area.
 constexpr size_t kHdrChunks = 0, kHdrExit = 4, kHdrFlags = 8, kHdrDone = 12, kHdrErr = 16,
-                 kHdrEpoch = 24, kHdrClaim = 28;
+                 kHdrEpoch = 24, kHdrClaim = 28, kHdrValidErr = 32;
 constexpr size_t kHdrResult = 64;   // result slot (used where no caller slot exists)
 constexpr size_t kHeaderBytes = 256;
 

@@ -33,7 +33,9 @@ def ctx(request):
     torch.cuda.init()
     h = gbu.gbu_create(0)
     small = gbu.GBU_SMALL_MAX_CHUNKS if request.param == "small" else 0
-    assert gbu.gbu_set_tune(h, 1, 0, small) == gbu.GBU_OK
+    # the default shape pinned (12 KiB chunks; by size, inputs up to 1 MiB
+    # would take the 8 KiB shape)
+    assert gbu.gbu_set_tune(h, 1, 0, small, CHUNK, 256) == gbu.GBU_OK
     assert gbu.gbu_get_tune(h).small_chunks == small
     yield h
     gbu.gbu_destroy(h)
@@ -154,8 +156,28 @@ def test_other_shapes(shape):
         gbu.gbu_destroy(h)
 
 
+def test_call_shape_by_size():
+    import torch
+    torch.cuda.init()
+    h = gbu.gbu_create(0)
+    try:
+        for n, want in ((1, (8192, 256)), (4096, (8192, 256)), (1 << 20, (8192, 256)),
+                        ((1 << 20) + 1, (12288, 256)), (1 << 30, (12288, 256))):
+            t = gbu.gbu_call_shape(h, n)
+            assert (t.chunk_bytes, t.compute_threads) == want, n
+            assert t.small_chunks == gbu.GBU_SMALL_MAX_CHUNKS
+        assert gbu.gbu_set_tune(h, 4, 0, 2, 24576, 512) == gbu.GBU_OK
+        t = gbu.gbu_call_shape(h, 100)
+        assert (t.look_width, t.small_chunks, t.chunk_bytes, t.compute_threads) == (4, 2, 24576, 512)
+    finally:
+        gbu.gbu_destroy(h)
+
+
 def test_one_launch_per_call(ctx):
     t8 = textgen.generate("latin", 2 * CHUNK, textgen.UTF8, seed=151).data
     before = gbu.gbu_kernel_launch_count()
     check_u8(ctx, t8)       # transcode, length, validation
-    assert gbu.gbu_kernel_launch_count() == before + 3
+    # one launch each on the one-launch path; beyond it a validation is the
+    # streaming kernel plus the result kernel
+    small = gbu.gbu_get_tune(ctx).small_chunks > 0
+    assert gbu.gbu_kernel_launch_count() == before + (3 if small else 4)

@@ -87,7 +87,7 @@ def parse():
                     help="batched: scale the string lengths so that they add up to this many "
                          "bytes (0: unscaled, log-uniform 16 B - 1 MiB)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--batch-strings", type=int, default=20_000,
+    ap.add_argument("--batch-strings", type=int, default=50_000,
                     help="single: strings of the batched measurement in the default line")
     ap.add_argument("--serve-rates", default="0.1,0.25,0.5,0.75,1.0",
                     help="single: load fractions of the serving measurement in the default line")

@@ -1015,7 +1015,9 @@ constexpr int kClaim = GBU_CLAIM;
 #endif
 constexpr int kLbSlots = GBU_LB_SLOTS;
 
-template <bool kWrite, int kLook, bool kAnyBE>
+// kIn: the input encoding of every item when known at launch (1 UTF-8, 2
+// UTF-16; the other direction's code is then not in the kernel), 0 any.
+template <bool kWrite, int kLook, bool kAnyBE, int kIn = 0>
 __global__ void __launch_bounds__(kBlock, kMinBlocks)
 transcode_kernel(const Job J)
 {
@@ -1295,7 +1297,7 @@ transcode_kernel(const Job J)
         }
         const int64_t lo = I.head, hi = (int64_t)I.head + (int64_t)I.n;
         const uint32_t k = c - I.chunk_base;
-        const bool u16 = (I.op & kOpUtf16) != 0;
+        const bool u16 = kIn == 2 || (kIn == 0 && (I.op & kOpUtf16) != 0);
         const bool be = kAnyBE && (I.op & kOpBE);
         bool interior;
         int64_t vt;
@@ -1546,22 +1548,32 @@ size_t job_smem_bytes(bool write)
 }
 
 // Every instantiation of the kernel: (write, look-back width, whether any
-// item is UTF-16BE; the UTF-16LE-only kernels carry no byte-order code).
+// item is UTF-16BE; the UTF-16LE-only kernels carry no byte-order code; for
+// little-endian transcoding of one encoding at the default look-back width,
+// kernels with that encoding's code only, half the code to fetch).
+#ifndef GBU_DIR_SPLIT
+#define GBU_DIR_SPLIT 1
+#endif
 template <bool W, int L>
-const void *kernel_fn(bool be)
+const void *kernel_fn(bool be, int in)
 {
+    if constexpr (W && L == GBU_DEFAULT_LOOK && GBU_DIR_SPLIT) {
+        if (!be && in == 1) return reinterpret_cast<const void *>(&transcode_kernel<W, L, false, 1>);
+        if (!be && in == 2) return reinterpret_cast<const void *>(&transcode_kernel<W, L, false, 2>);
+    }
     return be ? reinterpret_cast<const void *>(&transcode_kernel<W, L, true>)
               : reinterpret_cast<const void *>(&transcode_kernel<W, L, false>);
 }
 
-const void *kernel_for(bool write, int look, bool be)
+// in: 1 / 2 when every item's input is UTF-8 / UTF-16, else 0
+const void *kernel_for(bool write, int look, bool be, int in = 0)
 {
     switch (look) {
-    case 1: return write ? kernel_fn<true, 1>(be) : kernel_fn<false, 1>(be);
-    case 2: return write ? kernel_fn<true, 2>(be) : kernel_fn<false, 2>(be);
-    case 8: return write ? kernel_fn<true, 8>(be) : kernel_fn<false, 8>(be);
-    case 16: return write ? kernel_fn<true, 16>(be) : kernel_fn<false, 16>(be);
-    default: return write ? kernel_fn<true, 4>(be) : kernel_fn<false, 4>(be);
+    case 1: return write ? kernel_fn<true, 1>(be, in) : kernel_fn<false, 1>(be, in);
+    case 2: return write ? kernel_fn<true, 2>(be, in) : kernel_fn<false, 2>(be, in);
+    case 8: return write ? kernel_fn<true, 8>(be, in) : kernel_fn<false, 8>(be, in);
+    case 16: return write ? kernel_fn<true, 16>(be, in) : kernel_fn<false, 16>(be, in);
+    default: return write ? kernel_fn<true, 4>(be, in) : kernel_fn<false, 4>(be, in);
     }
 }
 
@@ -1575,10 +1587,11 @@ int job_max_ctas_per_sm(int device)
     for (const int look : kLookWidths)
         for (int w = 0; w < 2; w++)
             for (int be = 0; be < 2; be++)
-                if (cudaFuncSetAttribute(kernel_for(w != 0, look, be != 0),
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)job_smem_bytes(w != 0)) != cudaSuccess)
-                    return 0;
+                for (int in = 0; in < 3; in++)
+                    if (cudaFuncSetAttribute(kernel_for(w != 0, look, be != 0, in),
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)job_smem_bytes(w != 0)) != cudaSuccess)
+                        return 0;
     for (int be = 0; be < 2; be++)
         if (cudaFuncSetAttribute(small_fn<true>(be != 0), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kSmallSmem) != cudaSuccess ||
@@ -1605,7 +1618,9 @@ int job_grid(int device, const Tune &t)
 cudaError_t launch_job(const Job &J, bool write, int grid, cudaStream_t stream, int look, bool be)
 {
     void *args[] = {const_cast<Job *>(&J)};
-    return cudaLaunchKernel(kernel_for(write, look, be), dim3(grid), dim3(kBlock), args,
+    // a single input: the kernel of its encoding
+    const int in = J.items ? 0 : ((J.item0.op & kOpUtf16) ? 2 : 1);
+    return cudaLaunchKernel(kernel_for(write, look, be, in), dim3(grid), dim3(kBlock), args,
                             job_smem_bytes(write), stream);
 }
 

@@ -135,11 +135,16 @@ def measured_peak():
 
 
 def source_hash(kernel: str) -> str:
+    """Hash of the kernel's sources without their // comments and blank lines
+    (a comment edit does not change the kernel the counters were taken on)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2212_05098_gb300", "csrc")
     for name in (*KERNEL_SRC[kernel], "common.cuh", "kernels.h"):
-        with open(os.path.join(d, name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(d, name), encoding="utf-8") as f:
+            for line in f:
+                code = line.split("//", 1)[0].rstrip()
+                if code:
+                    h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 

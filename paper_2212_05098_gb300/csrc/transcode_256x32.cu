@@ -1,5 +1,5 @@
 // The transcoding kernels with 256 compute threads of 32 input bytes each
-// (8 KiB chunks), compiled for 2 resident CTA(s) per SM.
+// (8 KiB chunks), compiled for 2 resident CTAs per SM.
 #define GBU_THREADS 256
 #define GBU_BPT 32
 #define GBU_MIN_BLOCKS 2

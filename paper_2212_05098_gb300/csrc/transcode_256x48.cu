@@ -1,5 +1,5 @@
 // The transcoding kernels with 256 compute threads of 48 input bytes each
-// (12 KiB chunks), compiled for 2 resident CTA(s) per SM.
+// (12 KiB chunks), compiled for 2 resident CTAs per SM.
 #define GBU_THREADS 256
 #define GBU_BPT 48
 #define GBU_MIN_BLOCKS 2

@@ -1,5 +1,5 @@
 // The transcoding kernels with 512 compute threads of 32 input bytes each
-// (16 KiB chunks), compiled for 1 resident CTA(s) per SM.
+// (16 KiB chunks), compiled for 1 resident CTA per SM.
 #define GBU_THREADS 512
 #define GBU_BPT 32
 #define GBU_MIN_BLOCKS 1

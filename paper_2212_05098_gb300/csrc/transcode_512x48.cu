@@ -1,5 +1,5 @@
 // The transcoding kernels with 512 compute threads of 48 input bytes each
-// (24 KiB chunks), compiled for 1 resident CTA(s) per SM.
+// (24 KiB chunks), compiled for 1 resident CTA per SM.
 #define GBU_THREADS 512
 #define GBU_BPT 48
 #define GBU_MIN_BLOCKS 1

@@ -2,10 +2,11 @@
 // and Sec. 7) over a job of one or more inputs.
 //
 // Work decomposition. Every input ("item") is cut into chunks of kChunkBytes
-// input bytes (12 KiB: 48 bytes per compute thread); the chunks of all items
-// of a job are numbered globally and claimed in order from a counter by a
-// persistent grid (two CTAs per SM). A CTA has kThreads compute threads, a
-// producer warp and a look-back warp:
+// input bytes (kBPT bytes per compute thread; 12 KiB in the default shape of
+// 256 threads x 48 bytes); the chunks of all items of a job are numbered
+// globally and claimed in order from a counter by a persistent grid
+// (kMinBlocks CTAs per SM). A CTA has kThreads compute threads, a producer
+// warp and a look-back warp:
 //   * the producer (one lane) claims each chunk just ahead of its processing
 //     (once the compute warps have counted the chunk before it, so that the
 //     chunks of all CTAs are processed about in the order of their numbers)
@@ -15,7 +16,8 @@
 //     warp has arrived on its "empty" mbarrier, after the producer has
 //     recorded the chunk's first error and counted the chunk done;
 //   * the compute threads classify a chunk (thread t owns input bytes
-//     [48t, 48t + 48)), count its output and scan the counts across the CTA;
+//     [kBPT t, kBPT t + kBPT)), count its output and scan the counts across
+//     the CTA;
 //     thread 0 publishes the chunk's aggregate for the decoupled look-back;
 //   * the look-back warp looks back for the chunk's offset, several chunks at
 //     a time, publishes the inclusive prefix and hands the offset back;
@@ -26,6 +28,10 @@
 // at two CTA barriers per chunk: the scan's, which also tells every thread
 // whether any wait gave up, and the one that frees the staging buffer after
 // the write-out.
+//
+// Inputs of a few chunks take a one-launch cluster kernel instead (one CTA
+// per chunk, the same chunk body, aggregates exchanged through distributed
+// shared memory; see "One-launch path" below).
 //
 // Ownership: a UTF-8 unit belongs to the thread holding its end position
 // (see the UTF-8 section below); a UTF-16 surrogate pair is split between

@@ -181,3 +181,38 @@ def test_one_launch_per_call(ctx):
     # streaming kernel plus the result kernel
     small = gbu.gbu_get_tune(ctx).small_chunks > 0
     assert gbu.gbu_kernel_launch_count() == before + (3 if small else 4)
+
+
+def test_concurrent_streams():
+    """One-launch calls on several streams at once (they share no scratch):
+    every result and output equals the oracle's."""
+    import torch
+    torch.cuda.init()
+    h = gbu.gbu_create(0)
+    try:
+        streams = [torch.cuda.Stream() for _ in range(4)]
+        cases = []
+        for i in range(32):
+            n = 100 + 2000 * i      # all within the one-launch path (8 chunks of 8 KiB)
+            d = textgen.generate(["mix", "emoji", "cjk", "cyrillic"][i % 4], n, textgen.UTF8,
+                                 seed=210 + i).data
+            if i % 5 == 4:
+                d = textgen.mutate(d, 1, seed=260 + i)
+            din = torch.from_numpy(np.array(d, copy=True)).cuda()
+            dout = torch.zeros(2 * n + 16, dtype=torch.uint8, device="cuda")
+            res = torch.zeros(4, dtype=torch.int64, device="cuda")
+            cases.append((d, din, dout, res))
+        torch.cuda.synchronize()
+        for i, (d, din, dout, res) in enumerate(cases):
+            s = streams[i % len(streams)]
+            assert gbu.gbu_utf8_to_utf16le_async(h, din.data_ptr(), d.size, dout.data_ptr(), d.size,
+                                                 res.data_ptr(), s.cuda_stream) == gbu.GBU_OK
+        torch.cuda.synchronize()
+        for d, din, dout, res in cases:
+            ref, ref_out = oracle.utf8_to_utf16le(d)
+            r = res.cpu().numpy()
+            assert (int(r[0]) & 0xFFFFFFFF, int(r[1]), int(r[2])) == triple(ref)
+            n = min(ref.out_len, d.size)
+            assert np.array_equal(dout.cpu().numpy()[: 2 * n].view("<u2"), ref_out[:n])
+    finally:
+        gbu.gbu_destroy(h)

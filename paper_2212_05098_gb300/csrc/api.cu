@@ -105,6 +105,7 @@ struct gbu_ctx {
     uint64_t items_cap = 0, chunk_map_cap = 0;
     uint32_t batch_items = 0, batch_chunks = 0;
     bool batch_write = false, batch_be = false;
+    int batch_in = 0;                 // 1 / 2: every item's input is UTF-8 / UTF-16, else 0
     cudaStream_t capture_stream = nullptr;
     cudaGraphExec_t graph = nullptr;
     gbu::Tune tune;                   // launch parameters of every call on the context
@@ -281,7 +282,8 @@ int32_t enqueue(gbu_ctx *c, Op op, const void *in, uint64_t n, void *out, uint64
     int grid = V.grid(c->device, c->tune);
     if (grid <= 0) return GBU_DEVICE_ERROR;
     if ((uint32_t)grid > J.total_chunks) grid = (int)J.total_chunks;
-    const cudaError_t e = V.launch_job(J, write, grid, stream, c->tune.look, big_endian(op));
+    const cudaError_t e =
+        V.launch_job(J, write, grid, stream, c->tune.look, big_endian(op), utf16 ? 2 : 1);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     if (!ok(e)) {
         c->dirty = true;
@@ -793,11 +795,12 @@ static int32_t plan_batch(gbu_ctx *c, cudaStream_t s)
     const int vi = c->tune.variant >= 0 ? c->tune.variant : 0;
     const Variant &V = variant(vi);
     uint64_t chunks = 0;
-    bool any_write = false, any_be = false;
+    bool any_write = false, any_be = false, any8 = false, any16 = false;
     for (uint32_t i = 0; i < count; i++) {
         const gbu_batch_item &b = items[i];
         any_write |= op_writes(b.op);
         any_be |= op_big_endian(b.op);
+        (op_utf16_in(b.op) ? any16 : any8) = true;
         chunks += chunks_of(V, b.in, b.n, op_utf16_in(b.op));
     }
     c->batch_items = 0;
@@ -834,6 +837,7 @@ static int32_t plan_batch(gbu_ctx *c, cudaStream_t s)
     c->batch_chunks = (uint32_t)chunks;
     c->batch_write = any_write;
     c->batch_be = any_be;
+    c->batch_in = any8 && !any16 ? 1 : (any16 && !any8 ? 2 : 0);
     c->batch_variant = vi;
     if (c->graph) {
         cudaGraphExecDestroy(c->graph);
@@ -891,7 +895,8 @@ static int32_t batch_enqueue(gbu_ctx *c, cudaStream_t s, bool counted = true)
     int grid = V.grid(c->device, c->tune);
     if (grid <= 0) return GBU_DEVICE_ERROR;
     if ((uint32_t)grid > J.total_chunks) grid = (int)J.total_chunks;
-    const cudaError_t e = V.launch_job(J, c->batch_write, grid, s, c->tune.look, c->batch_be);
+    const cudaError_t e =
+        V.launch_job(J, c->batch_write, grid, s, c->tune.look, c->batch_be, c->batch_in);
     if (counted) g_launches.fetch_add(1, std::memory_order_relaxed);
     return ok(e) ? GBU_OK : GBU_DEVICE_ERROR;
 }

@@ -51,7 +51,10 @@ struct Tune {
 //                    per device; 0 on failure);
 //   grid             persistent grid for a tuning (every CTA resident);
 //   launch_job       the persistent kernel over a job (`be`: the job holds
-//                    UTF-16BE items, which selects a kernel with byte swaps);
+//                    UTF-16BE items, which selects a kernel with byte swaps;
+//                    `in`: 1 / 2 when every item's input is UTF-8 / UTF-16,
+//                    which may select a kernel with that direction's code
+//                    only, 0 otherwise);
 //   launch_small     the one-launch cluster kernel over one item of at most
 //                    kSmallMaxChunks chunks.
 struct Variant {
@@ -65,7 +68,7 @@ struct Variant {
     int (*max_ctas_per_sm)(int device);
     int (*grid)(int device, const Tune &t);
     cudaError_t (*launch_job)(const Job &J, bool write, int grid, cudaStream_t stream, int look,
-                              bool be);
+                              bool be, int in);
     cudaError_t (*launch_small)(const Item &I, bool write, bool validate, cudaStream_t stream);
 };
 

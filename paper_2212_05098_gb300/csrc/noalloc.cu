@@ -136,7 +136,7 @@ extern "C" gbu_result gbu_utf8_to_utf16le_noalloc(const uint8_t *d_in, uint64_t 
     J.err_prefix = J.status + kNoAllocChunks;
     J.item0.result = reinterpret_cast<ResultSlot *>(base + kHdrResult);
     const int grid = (uint32_t)max_grid > J.total_chunks ? (int)J.total_chunks : max_grid;
-    if (V.launch_job(J, true, grid, s, GBU_DEFAULT_LOOK, false) != cudaSuccess)
+    if (V.launch_job(J, true, grid, s, GBU_DEFAULT_LOOK, false, 1) != cudaSuccess)
         return fail(GBU_DEVICE_ERROR);
     note_launch();
     if (cudaMemcpyAsync(&r, base + kHdrResult, sizeof r, cudaMemcpyDeviceToHost, s) != cudaSuccess ||

@@ -1621,11 +1621,10 @@ int job_grid(int device, const Tune &t)
     return g_sms[device] * use;
 }
 
-cudaError_t launch_job(const Job &J, bool write, int grid, cudaStream_t stream, int look, bool be)
+cudaError_t launch_job(const Job &J, bool write, int grid, cudaStream_t stream, int look, bool be,
+                       int in)
 {
     void *args[] = {const_cast<Job *>(&J)};
-    // a single input: the kernel of its encoding
-    const int in = J.items ? 0 : ((J.item0.op & kOpUtf16) ? 2 : 1);
     return cudaLaunchKernel(kernel_for(write, look, be, in), dim3(grid), dim3(kBlock), args,
                             job_smem_bytes(write), stream);
 }

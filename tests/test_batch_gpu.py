@@ -337,3 +337,24 @@ def test_batch_big_endian_ops(ctx):
                 (ref.status, ref.in_offset, ref.out_len), i
             if out is not None:
                 assert np.array_equal(d_out[: out.size].cpu().numpy(), out), i
+
+
+@pytest.mark.parametrize("ops", [(0, 2), (1, 3), (0,), (1,)])
+def test_single_encoding_batches(ctx, ops):
+    """Batches whose items all read one encoding (they run the kernel with
+    that direction's code only), transcoding and length items mixed."""
+    rng = np.random.default_rng(95 + ops[0] + 10 * len(ops))
+    cases = []
+    for i in range(40):
+        op, data, cap = _case(rng, 1500 + 50 * ops[0] + i)
+        want_op = ops[i % len(ops)]
+        if (op in (1, 3)) != (want_op in (1, 3)):   # re-draw in the wanted encoding
+            enc = textgen.UTF16 if want_op in (1, 3) else textgen.UTF8
+            n = max(2, data.size)
+            data = textgen.generate("emoji", n + (n & 1), enc, seed=1700 + i).data
+            cap = None
+        cases.append((want_op, data, cap if want_op <= 1 else None))
+    b = Batch(cases, rng)
+    assert gbu.gbu_batch_plan(ctx, b.items, b.res.data_ptr(), 0) == gbu.GBU_OK
+    _run(ctx, b, gbu.gbu_batch_launch)
+    _run(ctx, b, gbu.gbu_batch_launch_graph)

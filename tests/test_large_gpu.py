@@ -4,9 +4,10 @@ positions above 2^32 end to end, against the oracle.
 - UTF-8 -> UTF-16LE of 4.6 GB of mix-profile text: the whole output compared
   with the oracle's; then one invalid byte planted 4.4 GB in: the transcoding,
   length and validation calls report the oracle's kind, offset and prefix.
-- UTF-16LE -> UTF-8 of 2.25 G units (4.5 GB): result triple against the oracle's
-  length call, and the output's tail against the oracle run on the last
-  4 MiB of the input (cut at a unit that is not a low surrogate).
+- UTF-16LE -> UTF-8 of 2.25 G units of CJK-like text (4.5 GB in, 6.3 GB
+  out): result triple against the oracle's length call, and the output's
+  tail against the oracle run on the last 4 MiB of the input (cut at a unit
+  that is not a low surrogate).
 """
 import numpy as np
 import pytest
@@ -62,7 +63,7 @@ def test_utf8_beyond_4gib(env):
 
 def test_utf16_beyond_4gib(env):
     torch, pool, ctx = env
-    t = textgen.generate("emoji", 2 * N16, textgen.UTF16, seed=301, executor=pool,
+    t = textgen.generate("cjk", 2 * N16, textgen.UTF16, seed=301, executor=pool,
                          keep_cps=False, keep_lens=False).data
     want = oracle.utf8_length_from_utf16le(t)
     assert want.status == gbu.GBU_OK and want.out_len > (1 << 32)

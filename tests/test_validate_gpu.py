@@ -107,3 +107,32 @@ def test_two_launches_and_reuse(ctx):
     for data in (bad, t, bad, t):           # the error word is reset by every call
         _check8(ctx, data, 0)
     assert gbu.gbu_kernel_launch_count() == before + 8
+
+
+def test_async_results_in_device_memory(ctx):
+    """The asynchronous validation calls on the streaming kernel, results in
+    device memory, one call after another on a stream."""
+    import torch
+    s = torch.cuda.Stream()
+    res = torch.zeros((6, 4), dtype=torch.int64, device="cuda")
+    datas, wants = [], []
+    for i in range(6):
+        t = textgen.generate(["mix", "cjk", "emoji"][i % 3], N + 1000 * i,
+                             textgen.UTF8 if i % 2 == 0 else textgen.UTF16, seed=220 + i).data
+        if i >= 3:
+            t = textgen.mutate(t, 1, seed=230 + i)
+        datas.append(DevIn(t, 2 * i))
+        wants.append(oracle.utf16_length_from_utf8(t) if i % 2 == 0
+                     else oracle.utf8_length_from_utf16le(t))
+    torch.cuda.synchronize()
+    for i, d in enumerate(datas):
+        if i % 2 == 0:
+            st = gbu.gbu_validate_utf8_async(ctx, d.ptr, d.nbytes, res[i].data_ptr(), s.cuda_stream)
+        else:
+            st = gbu.gbu_validate_utf16le_async(ctx, d.ptr, d.nbytes // 2, res[i].data_ptr(),
+                                                s.cuda_stream)
+        assert st == gbu.GBU_OK
+    s.synchronize()
+    h = res.cpu().numpy()
+    for i, w in enumerate(wants):
+        assert (int(h[i, 0]) & 0xFFFFFFFF, int(h[i, 1]), int(h[i, 2])) == (w.status, w.in_offset, 0)

@@ -105,7 +105,15 @@ struct gbu_ctx {
     uint64_t items_cap = 0, chunk_map_cap = 0;
     uint32_t batch_items = 0, batch_chunks = 0;
     bool batch_write = false, batch_be = false;
-    int batch_in = 0;                 // 1 / 2: every item's input is UTF-8 / UTF-16, else 0
+    // the persistent jobs of a batch: one per input encoding (UTF-8, UTF-16),
+    // each numbering its own chunks from 0 at chunk_item[grp_start[g]]
+    uint32_t grp_start[2] = {0, 0}, grp_chunks[2] = {0, 0};
+    int grp_in[2] = {0, 0};
+    bool grp_be[2] = {false, false}, grp_write[2] = {false, false};
+    // the batch's one-chunk items, run one CTA each apart from the persistent job
+    gbu::Item *d_small = nullptr, *h_small = nullptr;
+    uint64_t small_cap = 0;
+    uint32_t batch_small = 0;
     cudaStream_t capture_stream = nullptr;
     cudaGraphExec_t graph = nullptr;
     gbu::Tune tune;                   // launch parameters of every call on the context
@@ -347,6 +355,8 @@ void gbu_destroy(gbu_ctx *c)
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     if (c->d_items) cudaFree(c->d_items);
     if (c->h_items) cudaFreeHost(c->h_items);
+    if (c->d_small) cudaFree(c->d_small);
+    if (c->h_small) cudaFreeHost(c->h_small);
     if (c->d_chunk_item) cudaFree(c->d_chunk_item);
     if (c->h_chunk_item) cudaFreeHost(c->h_chunk_item);
     if (c->d_item_err) cudaFree(c->d_item_err);
@@ -758,12 +768,17 @@ static bool grow_batch(gbu_ctx *c, uint64_t items, uint64_t chunks)
         while (want < items) want *= 2;
         if (c->d_items) cudaFree(c->d_items);
         if (c->h_items) cudaFreeHost(c->h_items);
+        if (c->d_small) cudaFree(c->d_small);
+        if (c->h_small) cudaFreeHost(c->h_small);
         if (c->d_item_err) cudaFree(c->d_item_err);
         if (c->d_item_done) cudaFree(c->d_item_done);
         c->d_items = nullptr; c->h_items = nullptr; c->d_item_err = nullptr; c->d_item_done = nullptr;
+        c->d_small = nullptr; c->h_small = nullptr;
         c->items_cap = 0;
         if (!ok(cudaMalloc(&c->d_items, want * sizeof(Item))) ||
             !ok(cudaHostAlloc(&c->h_items, want * sizeof(Item), cudaHostAllocDefault)) ||
+            !ok(cudaMalloc(&c->d_small, want * sizeof(Item))) ||
+            !ok(cudaHostAlloc(&c->h_small, want * sizeof(Item), cudaHostAllocDefault)) ||
             !ok(cudaMalloc(&c->d_item_err, want * 8)) || !ok(cudaMalloc(&c->d_item_done, want * 4)))
             return false;
         c->items_cap = want;
@@ -785,6 +800,17 @@ static bool grow_batch(gbu_ctx *c, uint64_t items, uint64_t chunks)
 
 }  // extern "C"
 
+#ifndef GBU_BATCH_SMALL
+#define GBU_BATCH_SMALL 1
+#endif
+constexpr bool kBatchSmall = GBU_BATCH_SMALL != 0;
+// A batch with items of both input encodings runs one persistent job per
+// encoding, each on the kernel with that direction's code only.
+#ifndef GBU_BATCH_SPLIT
+#define GBU_BATCH_SPLIT 1
+#endif
+constexpr bool kBatchSplit = GBU_BATCH_SPLIT != 0;
+
 // Count the chunks of the context's batch for its kernel shape (the pinned
 // one, else the default), number them operation by operation, and copy the
 // descriptors to the device. The caller has validated the items.
@@ -795,13 +821,13 @@ static int32_t plan_batch(gbu_ctx *c, cudaStream_t s)
     const int vi = c->tune.variant >= 0 ? c->tune.variant : 0;
     const Variant &V = variant(vi);
     uint64_t chunks = 0;
-    bool any_write = false, any_be = false, any8 = false, any16 = false;
+    bool any_write = false, any_be = false;
     for (uint32_t i = 0; i < count; i++) {
         const gbu_batch_item &b = items[i];
         any_write |= op_writes(b.op);
         any_be |= op_big_endian(b.op);
-        (op_utf16_in(b.op) ? any16 : any8) = true;
-        chunks += chunks_of(V, b.in, b.n, op_utf16_in(b.op));
+        const uint64_t k = chunks_of(V, b.in, b.n, op_utf16_in(b.op));
+        if (k > 1 || !kBatchSmall) chunks += k;   // one-chunk items run apart
     }
     c->batch_items = 0;
     if (chunks >= (1ull << 31)) return GBU_INVALID_ARG;   // the claim counter may run past the end
@@ -809,11 +835,15 @@ static int32_t plan_batch(gbu_ctx *c, cudaStream_t s)
     if (!grow_batch(c, count ? count : 1, chunks ? chunks : 1)) return GBU_DEVICE_ERROR;
     // Chunks are numbered operation by operation (items keep their index and
     // result slot): a CTA then mostly runs one code path at a time, which
-    // keeps the instruction cache warm.
+    // keeps the instruction cache warm. With kBatchSplit the UTF-8-input and
+    // UTF-16-input items form two jobs, each numbered from 0.
     uint32_t base = 0;
     // Within an operation, items with more chunks first: the last chunks
-    // handed out are then short independent items, which end together
-    // (+3 % on 50,000 log-uniform strings against the callers' order).
+    // handed out are then the shortest of the persistent job's items (+3 %
+    // on 50,000 log-uniform strings against the callers' order). One-chunk
+    // items go to the one-CTA-per-item kernel instead: in the persistent
+    // job each would pay a chunk iteration's fixed costs (claim, descriptor
+    // loads, TMA hand-off, barriers, deferred write-out) for a few bytes.
     std::vector<uint32_t> order(count);
     std::vector<uint64_t> nch(count);
     for (uint32_t i = 0; i < count; i++) {
@@ -822,23 +852,48 @@ static int32_t plan_batch(gbu_ctx *c, cudaStream_t s)
     }
     std::stable_sort(order.begin(), order.end(),
                      [&](uint32_t a, uint32_t b) { return nch[a] > nch[b]; });
-    for (int op = GBU_OP_UTF8_TO_UTF16LE; op <= GBU_OP_UTF8_LENGTH_FROM_UTF16BE; op++) {
-        for (const uint32_t i : order) {
-            const gbu_batch_item &b = items[i];
-            if (b.op != op) continue;
-            Item I = V.make_item(b.in, b.n, op_utf16_in(b.op), b.out, b.cap, op_writes(b.op),
-                                 reinterpret_cast<ResultSlot *>(c->batch_results + i), base,
-                                 op_big_endian(b.op));
-            c->h_items[i] = I;
-            for (uint32_t k = 0; k < I.nchunks; k++) c->h_chunk_item[base + k] = i;
-            base += I.nchunks;
+    uint32_t nsmall = 0, pos = 0;   // pos: next entry of the chunk -> item map
+    const int ngrp = kBatchSplit ? 2 : 1;
+    for (int g = 0; g < ngrp; g++) {
+        c->grp_start[g] = pos;
+        base = 0;   // each job numbers its chunks from 0
+        bool g8 = false, g16 = false, gbe = false, gw = false;
+        for (int op = GBU_OP_UTF8_TO_UTF16LE; op <= GBU_OP_UTF8_LENGTH_FROM_UTF16BE; op++) {
+            if (kBatchSplit && (op_utf16_in(op) ? 1 : 0) != g) continue;
+            for (const uint32_t i : order) {
+                const gbu_batch_item &b = items[i];
+                if (b.op != op) continue;
+                const bool big = nch[i] > 1 || !kBatchSmall;
+                Item I = V.make_item(b.in, b.n, op_utf16_in(b.op), b.out, b.cap, op_writes(b.op),
+                                     reinterpret_cast<ResultSlot *>(c->batch_results + i),
+                                     big ? base : 0, op_big_endian(b.op));
+                c->h_items[i] = I;
+                if (!big) {
+                    c->h_small[nsmall++] = I;
+                    continue;
+                }
+                (op_utf16_in(b.op) ? g16 : g8) = true;
+                gbe |= op_big_endian(b.op);
+                gw |= op_writes(b.op);
+                for (uint32_t k = 0; k < I.nchunks; k++) c->h_chunk_item[pos + k] = i;
+                base += I.nchunks;
+                pos += I.nchunks;
+            }
         }
+        c->grp_chunks[g] = base;
+        c->grp_in[g] = g8 && !g16 ? 1 : (g16 && !g8 ? 2 : 0);
+        c->grp_be[g] = gbe;
+        c->grp_write[g] = gw;
     }
+    for (int g = ngrp; g < 2; g++) c->grp_chunks[g] = 0;
     int32_t st = ensure_scratch(c, chunks ? chunks : 1, s);
     if (st != GBU_OK) return st;
     if (count) {
         if (!ok(cudaMemcpyAsync(c->d_items, c->h_items, count * sizeof(Item), cudaMemcpyHostToDevice, s)) ||
-            !ok(cudaMemcpyAsync(c->d_chunk_item, c->h_chunk_item, chunks * 4, cudaMemcpyHostToDevice, s)) ||
+            (nsmall && !ok(cudaMemcpyAsync(c->d_small, c->h_small, nsmall * sizeof(Item),
+                                           cudaMemcpyHostToDevice, s))) ||
+            (chunks && !ok(cudaMemcpyAsync(c->d_chunk_item, c->h_chunk_item, chunks * 4,
+                                           cudaMemcpyHostToDevice, s))) ||
             !ok(cudaMemsetAsync(c->d_item_err, 0xFF, (size_t)count * 8, s)) ||
             !ok(cudaMemsetAsync(c->d_item_done, 0, (size_t)count * 4, s)) ||
             !ok(cudaStreamSynchronize(s)))
@@ -846,9 +901,9 @@ static int32_t plan_batch(gbu_ctx *c, cudaStream_t s)
     }
     c->batch_items = count;
     c->batch_chunks = (uint32_t)chunks;
+    c->batch_small = nsmall;
     c->batch_write = any_write;
     c->batch_be = any_be;
-    c->batch_in = any8 && !any16 ? 1 : (any16 && !any8 ? 2 : 0);
     c->batch_variant = vi;
     if (c->graph) {
         cudaGraphExecDestroy(c->graph);
@@ -893,23 +948,33 @@ int32_t gbu_batch_plan(gbu_ctx *c, const gbu_batch_item *items, uint32_t count,
 static int32_t batch_enqueue(gbu_ctx *c, cudaStream_t s, bool counted = true)
 {
     if (c->batch_items == 0) return GBU_OK;
-    Job J{};
-    J.items = c->d_items;
-    J.chunk_item = c->d_chunk_item;
-    J.num_items = c->batch_items;
-    J.total_chunks = c->batch_chunks;
-    attach_scratch(c, J);
-    J.item_err = c->d_item_err;
-    J.item_done = c->d_item_done;
-    J.wait_ns = c->wait_ns;
     const Variant &V = variant(c->batch_variant);
-    int grid = V.grid(c->device, c->tune);
-    if (grid <= 0) return GBU_DEVICE_ERROR;
-    if ((uint32_t)grid > J.total_chunks) grid = (int)J.total_chunks;
-    const cudaError_t e =
-        V.launch_job(J, c->batch_write, grid, s, c->tune.look, c->batch_be, c->batch_in);
-    if (counted) g_launches.fetch_add(1, std::memory_order_relaxed);
-    return ok(e) ? GBU_OK : GBU_DEVICE_ERROR;
+    if (c->batch_small) {
+        const cudaError_t e =
+            V.launch_small_items(c->d_small, c->batch_small, c->batch_write, c->batch_be, s);
+        if (counted) g_launches.fetch_add(1, std::memory_order_relaxed);
+        if (!ok(e)) return GBU_DEVICE_ERROR;
+    }
+    for (int g = 0; g < 2; g++) {
+        if (c->grp_chunks[g] == 0) continue;
+        Job J{};
+        J.items = c->d_items;
+        J.chunk_item = c->d_chunk_item + c->grp_start[g];
+        J.num_items = c->batch_items;
+        J.total_chunks = c->grp_chunks[g];
+        attach_scratch(c, J);
+        J.item_err = c->d_item_err;
+        J.item_done = c->d_item_done;
+        J.wait_ns = c->wait_ns;
+        int grid = V.grid(c->device, c->tune);
+        if (grid <= 0) return GBU_DEVICE_ERROR;
+        if ((uint32_t)grid > J.total_chunks) grid = (int)J.total_chunks;
+        const cudaError_t e = V.launch_job(J, c->grp_write[g], grid, s, c->tune.look,
+                                           c->grp_be[g], c->grp_in[g]);
+        if (counted) g_launches.fetch_add(1, std::memory_order_relaxed);
+        if (!ok(e)) return GBU_DEVICE_ERROR;
+    }
+    return GBU_OK;
 }
 
 int32_t gbu_batch_launch(gbu_ctx *c, void *stream)
@@ -954,7 +1019,10 @@ int32_t gbu_batch_launch_graph(gbu_ctx *c, void *stream)
         }
     }
     if (!ok(cudaGraphLaunch(c->graph, s))) return GBU_DEVICE_ERROR;
-    g_launches.fetch_add(1, std::memory_order_relaxed);   // the graph holds one kernel launch
+    // the graph holds the one-chunk items' kernel and the persistent kernel (either may be absent)
+    g_launches.fetch_add((c->batch_small ? 1 : 0) + (c->grp_chunks[0] ? 1 : 0) +
+                             (c->grp_chunks[1] ? 1 : 0),
+                         std::memory_order_relaxed);
     return GBU_OK;
 }
 

@@ -88,7 +88,10 @@ constexpr uint64_t kValueMask = (1ull << 40) - 1;
 constexpr uint64_t kWaitNs = 1000000000ull;   // 1 s
 // An mbarrier wait suspends the thread in hardware until the phase completes
 // or this many nanoseconds pass, then checks the clock and waits again.
-constexpr uint32_t kSuspendNs = 20000;
+#ifndef GBU_SUSPEND_NS
+#define GBU_SUSPEND_NS 20000
+#endif
+constexpr uint32_t kSuspendNs = GBU_SUSPEND_NS;
 // Look-back rounds that find a predecessor not ready: the first few re-read
 // at once (an L2 round trip paces them), later ones back off (ns).
 #ifndef GBU_LB_SLEEP_SHORT

@@ -56,7 +56,9 @@ struct Tune {
 //                    which may select a kernel with that direction's code
 //                    only, 0 otherwise);
 //   launch_small     the one-launch cluster kernel over one item of at most
-//                    kSmallMaxChunks chunks.
+//                    kSmallMaxChunks chunks;
+//   launch_small_items  one CTA per item over `count` one-chunk items (device
+//                    array; `any_be`: some item is UTF-16BE).
 struct Variant {
     int threads;
     int bpt;
@@ -70,6 +72,8 @@ struct Variant {
     cudaError_t (*launch_job)(const Job &J, bool write, int grid, cudaStream_t stream, int look,
                               bool be, int in);
     cudaError_t (*launch_small)(const Item &I, bool write, bool validate, cudaStream_t stream);
+    cudaError_t (*launch_small_items)(const Item *items, uint32_t count, bool write, bool any_be,
+                                      cudaStream_t stream);
 };
 
 // The compiled shapes (compute threads x bytes per thread).

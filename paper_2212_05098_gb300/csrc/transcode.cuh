@@ -1431,20 +1431,28 @@ __device__ __forceinline__ void st_cluster_u64(const void *local, uint32_t rank,
 
 constexpr size_t kSmallSmem = (size_t)kStageBytes + kOutBuf;
 
-// Grid = cluster = the item's chunks (1 .. kSmallMaxChunks); CTA k converts
-// chunk k. `validate`: the validation-only form (out_len reported as 0).
-template <bool kWrite, bool kBE>
-__global__ void __launch_bounds__(kThreads, 1) small_kernel(const Item I, uint32_t validate)
-{
-    extern __shared__ __align__(128) uint8_t dyn_smem[];
-    uint8_t *const stage = dyn_smem;
-    uint8_t *const obuf = dyn_smem + kStageBytes;
-    __shared__ uint32_t s_warp[kThreads / 32 + 1];
-    __shared__ uint32_t s_agg[kSmallMaxChunks];              // every chunk's output units
-    __shared__ unsigned long long s_key[kSmallMaxChunks];    // CTA 0: every chunk's first error
-    __shared__ unsigned long long s_err;
+// Static shared memory of a one-launch CTA (the same layout in every CTA of
+// a cluster, which the distributed shared-memory stores rely on).
+struct SmallSmem {
+    uint32_t warp[kThreads / 32 + 1];
+    uint32_t agg[kSmallMaxChunks];              // every chunk's output units
+    unsigned long long key[kSmallMaxChunks];    // CTA 0: every chunk's first error
+    unsigned long long err;
+};
 
-    const uint32_t tid = threadIdx.x, k = blockIdx.x, nct = gridDim.x;
+// Chunk k of nct (the CTA's rank in its cluster) of item I: load, the chunk
+// body, the aggregates and first errors through the cluster, the output and
+// (CTA 0) the result. `validate`: the validation-only form (out_len 0).
+template <bool kWrite, bool kBE>
+__device__ __forceinline__ void small_body(const Item &I, uint32_t k, uint32_t nct,
+                                           uint32_t validate, SmallSmem &S, uint8_t *stage,
+                                           uint8_t *obuf)
+{
+    uint32_t *const s_warp = S.warp;
+    uint32_t *const s_agg = S.agg;
+    unsigned long long *const s_key = S.key;
+    unsigned long long &s_err = S.err;
+    const uint32_t tid = threadIdx.x;
     if (tid == 0) s_err = ~0ull;
     const bool u16 = (I.op & kOpUtf16) != 0;
     // the window of the persistent kernel's TMA load (16-byte aligned, whole
@@ -1536,7 +1544,31 @@ __global__ void __launch_bounds__(kThreads, 1) small_kernel(const Item I, uint32
     if (key != ~0ull)
         write_result(I, (int32_t)((key >> 15) & 0xFFu), key >> 23, prefix + (key & 0x7FFFu), v);
     else
-        write_result(I, (kWrite && total > I.cap) ? kOutputTooSmall : kOk, I.n, total, v);
+        write_result(I, ((I.op & kOpWrite) && total > I.cap) ? kOutputTooSmall : kOk, I.n, total, v);
+}
+
+// Grid = cluster = the item's chunks (1 .. kSmallMaxChunks); CTA k converts
+// chunk k. `validate`: the validation-only form (out_len reported as 0).
+template <bool kWrite, bool kBE>
+__global__ void __launch_bounds__(kThreads, 1) small_kernel(const Item I, uint32_t validate)
+{
+    extern __shared__ __align__(128) uint8_t dyn_smem[];
+    __shared__ SmallSmem S;
+    small_body<kWrite, kBE>(I, blockIdx.x, gridDim.x, validate, S, dyn_smem, dyn_smem + kStageBytes);
+}
+
+// A batch's one-chunk items, one CTA each (no cluster, no scratch): CTA b
+// converts items[b] and writes its result. kAnyBE: some item is UTF-16BE.
+template <bool kWrite, bool kAnyBE>
+__global__ void __launch_bounds__(kThreads, 1) small_items_kernel(const Item *items)
+{
+    extern __shared__ __align__(128) uint8_t dyn_smem[];
+    __shared__ SmallSmem S;
+    const Item I = items[blockIdx.x];
+    if (kAnyBE && (I.op & kOpBE))
+        small_body<kWrite, true>(I, 0, 1, 0, S, dyn_smem, dyn_smem + kStageBytes);
+    else
+        small_body<kWrite, false>(I, 0, 1, 0, S, dyn_smem, dyn_smem + kStageBytes);
 }
 
 template <bool W>
@@ -1544,6 +1576,13 @@ const void *small_fn(bool be)
 {
     return be ? reinterpret_cast<const void *>(&small_kernel<W, true>)
               : reinterpret_cast<const void *>(&small_kernel<W, false>);
+}
+
+template <bool W>
+const void *small_items_fn(bool any_be)
+{
+    return any_be ? reinterpret_cast<const void *>(&small_items_kernel<W, true>)
+                  : reinterpret_cast<const void *>(&small_items_kernel<W, false>);
 }
 
 int g_max_per_sm[64] = {0};
@@ -1605,7 +1644,11 @@ int job_max_ctas_per_sm(int device)
         if (cudaFuncSetAttribute(small_fn<true>(be != 0), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kSmallSmem) != cudaSuccess ||
             cudaFuncSetAttribute(small_fn<false>(be != 0), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kSmallSmem) != cudaSuccess)
+                                 (int)kSmallSmem) != cudaSuccess ||
+            cudaFuncSetAttribute(small_items_fn<true>(be != 0),
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmallSmem) != cudaSuccess ||
+            cudaFuncSetAttribute(small_items_fn<false>(be != 0),
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmallSmem) != cudaSuccess)
             return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel_for(true, GBU_DEFAULT_LOOK, false), kBlock,
                                                       job_smem_bytes(true)) != cudaSuccess ||
@@ -1660,6 +1703,21 @@ cudaError_t launch_small(const Item &I, bool write, bool validate, cudaStream_t 
     return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
+cudaError_t launch_small_items(const Item *items, uint32_t count, bool write, bool any_be,
+                               cudaStream_t stream)
+{
+    if (count == 0) return cudaSuccess;
+    if (kSmallSmem > 48 * 1024) {   // the attribute is set once per device
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || job_max_ctas_per_sm(dev) <= 0)
+            return cudaErrorInvalidValue;
+    }
+    const void *fn = write ? small_items_fn<true>(any_be) : small_items_fn<false>(any_be);
+    const Item *arg = items;
+    void *args[] = {&arg};
+    return cudaLaunchKernel(fn, dim3(count), dim3(kThreads), args, kSmallSmem, stream);
+}
+
 Item make_item(const void *in, uint64_t n, bool utf16, void *out, uint64_t cap, bool write,
                ResultSlot *result, uint32_t chunk_base, bool big_endian)
 {
@@ -1697,7 +1755,8 @@ const Variant &GBU_VARIANT_FN()
                               &GBU_VNS::job_max_ctas_per_sm,
                               &GBU_VNS::job_grid,
                               &GBU_VNS::launch_job,
-                              &GBU_VNS::launch_small};
+                              &GBU_VNS::launch_small,
+                              &GBU_VNS::launch_small_items};
     return v;
 }
 

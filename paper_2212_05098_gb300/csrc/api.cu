@@ -800,16 +800,12 @@ static bool grow_batch(gbu_ctx *c, uint64_t items, uint64_t chunks)
 
 }  // extern "C"
 
-#ifndef GBU_BATCH_SMALL
-#define GBU_BATCH_SMALL 1
-#endif
-constexpr bool kBatchSmall = GBU_BATCH_SMALL != 0;
-// A batch with items of both input encodings runs one persistent job per
-// encoding, each on the kernel with that direction's code only.
-#ifndef GBU_BATCH_SPLIT
-#define GBU_BATCH_SPLIT 1
-#endif
-constexpr bool kBatchSplit = GBU_BATCH_SPLIT != 0;
+// A large batch (at least kSpreadBytes of input) runs its one-chunk items in
+// a kernel of their own and the rest as one persistent job per input
+// encoding, each on the kernel with that direction's code only (+3 % on
+// 50,000 log-uniform strings); a smaller one (a served batch, say) runs as
+// one persistent job, since every extra launch adds to its latency.
+constexpr uint64_t kSpreadBytes = 512ull << 20;
 
 // Count the chunks of the context's batch for its kernel shape (the pinned
 // one, else the default), number them operation by operation, and copy the
@@ -822,12 +818,18 @@ static int32_t plan_batch(gbu_ctx *c, cudaStream_t s)
     const Variant &V = variant(vi);
     uint64_t chunks = 0;
     bool any_write = false, any_be = false;
+    uint64_t in_bytes = 0;
+    for (uint32_t i = 0; i < count; i++) {
+        const gbu_batch_item &b = items[i];
+        in_bytes += op_utf16_in(b.op) ? 2 * b.n : b.n;
+    }
+    const bool spread = in_bytes >= kSpreadBytes;
     for (uint32_t i = 0; i < count; i++) {
         const gbu_batch_item &b = items[i];
         any_write |= op_writes(b.op);
         any_be |= op_big_endian(b.op);
         const uint64_t k = chunks_of(V, b.in, b.n, op_utf16_in(b.op));
-        if (k > 1 || !kBatchSmall) chunks += k;   // one-chunk items run apart
+        if (k > 1 || !spread) chunks += k;   // one-chunk items run apart
     }
     c->batch_items = 0;
     if (chunks >= (1ull << 31)) return GBU_INVALID_ARG;   // the claim counter may run past the end
@@ -835,7 +837,7 @@ static int32_t plan_batch(gbu_ctx *c, cudaStream_t s)
     if (!grow_batch(c, count ? count : 1, chunks ? chunks : 1)) return GBU_DEVICE_ERROR;
     // Chunks are numbered operation by operation (items keep their index and
     // result slot): a CTA then mostly runs one code path at a time, which
-    // keeps the instruction cache warm. With kBatchSplit the UTF-8-input and
+    // keeps the instruction cache warm. In a large batch the UTF-8-input and
     // UTF-16-input items form two jobs, each numbered from 0.
     uint32_t base = 0;
     // Within an operation, items with more chunks first: the last chunks
@@ -853,17 +855,17 @@ static int32_t plan_batch(gbu_ctx *c, cudaStream_t s)
     std::stable_sort(order.begin(), order.end(),
                      [&](uint32_t a, uint32_t b) { return nch[a] > nch[b]; });
     uint32_t nsmall = 0, pos = 0;   // pos: next entry of the chunk -> item map
-    const int ngrp = kBatchSplit ? 2 : 1;
+    const int ngrp = spread ? 2 : 1;
     for (int g = 0; g < ngrp; g++) {
         c->grp_start[g] = pos;
         base = 0;   // each job numbers its chunks from 0
         bool g8 = false, g16 = false, gbe = false, gw = false;
         for (int op = GBU_OP_UTF8_TO_UTF16LE; op <= GBU_OP_UTF8_LENGTH_FROM_UTF16BE; op++) {
-            if (kBatchSplit && (op_utf16_in(op) ? 1 : 0) != g) continue;
+            if (spread && (op_utf16_in(op) ? 1 : 0) != g) continue;
             for (const uint32_t i : order) {
                 const gbu_batch_item &b = items[i];
                 if (b.op != op) continue;
-                const bool big = nch[i] > 1 || !kBatchSmall;
+                const bool big = nch[i] > 1 || !spread;
                 Item I = V.make_item(b.in, b.n, op_utf16_in(b.op), b.out, b.cap, op_writes(b.op),
                                      reinterpret_cast<ResultSlot *>(c->batch_results + i),
                                      big ? base : 0, op_big_endian(b.op));

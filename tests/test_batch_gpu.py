@@ -358,3 +358,30 @@ def test_single_encoding_batches(ctx, ops):
     assert gbu.gbu_batch_plan(ctx, b.items, b.res.data_ptr(), 0) == gbu.GBU_OK
     _run(ctx, b, gbu.gbu_batch_launch)
     _run(ctx, b, gbu.gbu_batch_launch_graph)
+
+
+def test_large_batch_spread(ctx):
+    """A batch of more than 512 MiB runs its one-chunk items in their own
+    kernel and the rest as one job per input encoding: every result and output
+    still equals the oracle's, with errors and small capacities in both."""
+    rng = np.random.default_rng(96)
+    cases = []
+    for i in range(44):                       # ~14 MB each, every operation
+        op = i % 4
+        enc = textgen.UTF16 if op in (1, 3) else textgen.UTF8
+        n = 13_000_000 + 7919 * i
+        data = textgen.generate(["cjk", "emoji", "mix", "cyrillic"][i % 4], n + (n & 1), enc,
+                                seed=1800 + i).data
+        if i % 5 == 0:
+            data = textgen.mutate(data, 1, seed=1900 + i)
+        cap = int(data.size // 3) if (op <= 1 and i % 7 == 3) else None
+        cases.append((op, data, cap))
+    for i in range(600):                      # short items, many of one chunk, some empty
+        cases.append(_case(rng, 2000 + i) if i % 3 else (i % 4, np.zeros(0, np.uint8), None))
+    b = Batch(cases, rng)
+    assert sum(c[1].size for c in cases) > (512 << 20)
+    assert gbu.gbu_batch_plan(ctx, b.items, b.res.data_ptr(), 0) == gbu.GBU_OK
+    before = gbu.gbu_kernel_launch_count()
+    _run(ctx, b, gbu.gbu_batch_launch, times=1)
+    assert gbu.gbu_kernel_launch_count() - before == 3   # one-chunk items + one job per encoding
+    _run(ctx, b, gbu.gbu_batch_launch_graph, times=1)

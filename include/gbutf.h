@@ -196,15 +196,18 @@ gbu_result gbu_utf8_to_utf16le_host(gbu_ctx *ctx, const uint8_t *h_in, uint64_t 
 gbu_result gbu_utf16le_to_utf8_host(gbu_ctx *ctx, const uint16_t *h_in, uint64_t n_units,
                                     uint8_t *h_out, uint64_t cap_bytes, void *stream);
 
-/* ---- Batches: many independent inputs in one persistent launch -------------
+/* ---- Batches: many independent inputs in one launch of the work ------------
  *
  * The paper transcodes one buffer per call; a batch runs many such calls (any
- * mix of directions and of transcoding / length-only) in ONE launch of the
- * persistent kernel: the chunks of all inputs are numbered consecutively
- * (grouped by operation, in item order within a group) and handed out in
- * order, every input keeps its own prefix scan, first error and
- * result, so each result equals that of the single-buffer call on the same
- * input. */
+ * mix of directions and of transcoding / length-only) together: the chunks of
+ * all inputs are numbered consecutively (grouped by operation, the items with
+ * the most chunks first within a group) and handed out in order to ONE
+ * launch of the persistent kernel; every input keeps its own prefix scan,
+ * first error and result, so each result equals that of the single-buffer
+ * call on the same input. A batch of at least 512 MiB of input instead runs
+ * its one-chunk items in a kernel of one CTA per item and the rest as one
+ * persistent launch per input encoding (up to three launches, in order on
+ * the stream; faster for large batches, more latency for small ones). */
 typedef enum gbu_op {
     GBU_OP_UTF8_TO_UTF16LE = 0,           /* as gbu_utf8_to_utf16le            */
     GBU_OP_UTF16LE_TO_UTF8 = 1,           /* as gbu_utf16le_to_utf8            */
@@ -235,9 +238,10 @@ typedef struct gbu_batch_item {
 int32_t gbu_batch_plan(gbu_ctx *ctx, const gbu_batch_item *items, uint32_t count,
                        gbu_result *results, void *stream);
 
-/* Enqueue one launch of the planned batch on `stream` (no host work, no
- * allocation; it may be captured into a CUDA graph by the caller). Results are
- * stored when the stream reaches the end of the work. */
+/* Enqueue the planned batch on `stream` (one launch, or up to three for a
+ * batch of 512 MiB or more; no host work, no allocation; it may be captured
+ * into a CUDA graph by the caller). Results are stored when the stream
+ * reaches the end of the work. */
 int32_t gbu_batch_launch(gbu_ctx *ctx, void *stream);
 
 /* Same, through a CUDA graph the context captures once per plan and replays

@@ -564,22 +564,35 @@ def main():
         e2e["link_bound"] = world * h2d / t_link / 1e9
         e2e["frac_of_link_bound"] = e2e["value"] / e2e["link_bound"]
 
-    # validation only (no output, no look-back), same buffers, 3 passes
+    # validation only (no output, no look-back), same buffers: one untimed
+    # pass, then 3 timed passes with an event between calls (per-buffer rates)
     vres = torch.zeros(4, dtype=torch.int64, device="cuda")
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def validate_call(c):
+        if c["dir"] == "utf8_to_utf16le":
+            gbu.gbu_validate_utf8_async(ctx.handle, c["d_in"].data_ptr(), c["n"],
+                                        vres.data_ptr(), sh)
+        else:
+            gbu.gbu_validate_utf16le_async(ctx.handle, c["d_in"].data_ptr(), c["n"],
+                                           vres.data_ptr(), sh)
+
     with torch.cuda.stream(stream):
-        e0.record(stream)
-        for _ in range(3):
-            for c in cases:
-                if c["dir"] == "utf8_to_utf16le":
-                    gbu.gbu_validate_utf8_async(ctx.handle, c["d_in"].data_ptr(), c["n"],
-                                                vres.data_ptr(), sh)
-                else:
-                    gbu.gbu_validate_utf16le_async(ctx.handle, c["d_in"].data_ptr(), c["n"],
-                                                   vres.data_ptr(), sh)
-        e1.record(stream)
+        for c in cases:
+            validate_call(c)
+        vev = [torch.cuda.Event(enable_timing=True) for _ in range(3 * len(cases) + 1)]
+        vev[0].record(stream)
+        for p in range(3):
+            for i, c in enumerate(cases):
+                validate_call(c)
+                vev[1 + p * len(cases) + i].record(stream)
     stream.synchronize()
-    validate_gbs = 3 * bytes_step / (e0.elapsed_time(e1) / 1e3) / 1e9
+    validate_gbs = 3 * bytes_step / (vev[0].elapsed_time(vev[-1]) / 1e3) / 1e9
+    validate_per_case = {}
+    for i, c in enumerate(cases):
+        ms = sum(vev[p * len(cases) + i].elapsed_time(vev[1 + p * len(cases) + i])
+                 for p in range(3))
+        enc = "utf8" if c["dir"] == "utf8_to_utf16le" else "utf16le"
+        validate_per_case[f"{c['profile']}/{enc}"] = 3 * c["data"].size / (ms / 1e3) / 1e9
 
     # ---- the batched launch, the serving loop and UTF-32 on the same device --
     extras = {}
@@ -637,6 +650,7 @@ def main():
             "per_buffer_output_bytes": {f"{c['profile']}/{c['dir']}":
                                         c["alg_bytes"] - c["data"].size for c in cases},
             "validate_only_input_gbs": validate_gbs,
+            "validate_only_per_buffer_gbs": validate_per_case,
             **extras,
             "cpu_baseline": cpu,
             "e2e": e2e,

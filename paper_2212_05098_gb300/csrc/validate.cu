@@ -4,10 +4,11 @@
 // shared memory and no barrier.
 //
 // Each thread checks kVB = 32 input bytes per step with two aligned 16-byte
-// loads. The lanes of a warp hold consecutive 32-byte blocks, so the 4 bytes
-// before and after a thread's block (the context its checks need) come from
-// the neighbouring lanes by shuffles, and from global memory at the two ends
-// of the warp. Bytes are counted from the 16-byte boundary at or before the
+// loads, issued one step ahead (the next step's loads are in flight while the
+// thread checks the current block). The lanes of a warp hold consecutive
+// 32-byte blocks, so the 4 bytes before and after a thread's block (the
+// context its checks need) come from the neighbouring lanes by shuffles, and
+// from global memory at the two ends of the warp. Bytes are counted from the 16-byte boundary at or before the
 // input ("virtual" positions); bytes outside the input read as zero, which
 // neither creates nor hides an error inside it, and no read leaves the
 // 16-byte blocks that hold input bytes.
@@ -35,6 +36,8 @@ namespace {
 constexpr int kVB = 32;          // input bytes per thread and step
 constexpr int kVW = kVB / 4;     // their 32-bit words
 constexpr int kVThreads = 256;   // threads per CTA
+constexpr int kV8Blocks = 4;     // resident CTAs per SM the UTF-8 kernel is compiled for
+constexpr int kV16Blocks = 6;    // and the UTF-16 kernels
 constexpr uint32_t kHi7 = 0x80808080u;
 
 __device__ __forceinline__ uint32_t ldg32(const uint8_t *p)
@@ -42,22 +45,39 @@ __device__ __forceinline__ uint32_t ldg32(const uint8_t *p)
     return __ldg(reinterpret_cast<const uint32_t *>(p));
 }
 
-// The thread's words at virtual byte v: w[1..kVW] its own, w[0] the 4 bytes
-// before, w[kVW + 1] the 4 bytes after (zero beyond the readable end endv, a
-// multiple of 16). Every lane of the warp calls it (shuffles).
-__device__ __forceinline__ void load_block(const uint8_t *in_al, uint64_t v, uint64_t endv,
-                                           uint32_t (&w)[kVW + 2])
+// A thread's loads for the block at virtual byte v: its 32 bytes, and at the
+// two ends of the warp the word beyond the warp's blocks (lane 0: the 4 bytes
+// before v, lane 31: the 4 bytes after its block). Nothing at or beyond the
+// readable end endv (a multiple of 16) is read; those bytes are zero.
+struct Raw {
+    uint4 a, b;
+    uint32_t edge;
+};
+
+__device__ __forceinline__ void fetch_block(const uint8_t *in_al, uint64_t v, uint64_t endv,
+                                            uint32_t lane, Raw &r)
 {
     const uint4 z = make_uint4(0, 0, 0, 0);
-    const uint4 a = v < endv ? __ldg(reinterpret_cast<const uint4 *>(in_al + v)) : z;
-    const uint4 b = v + 16 < endv ? __ldg(reinterpret_cast<const uint4 *>(in_al + v + 16)) : z;
-    w[1] = a.x; w[2] = a.y; w[3] = a.z; w[4] = a.w;
-    w[5] = b.x; w[6] = b.y; w[7] = b.z; w[8] = b.w;
-    const uint32_t lane = threadIdx.x & 31u;
+    r.a = v < endv ? __ldg(reinterpret_cast<const uint4 *>(in_al + v)) : z;
+    r.b = v + 16 < endv ? __ldg(reinterpret_cast<const uint4 *>(in_al + v + 16)) : z;
+    r.edge = 0u;
+    if (lane == 0)
+        r.edge = v >= 4 && v - 4 < endv ? ldg32(in_al + v - 4) : 0u;
+    else if (lane == 31)
+        r.edge = v + kVB < endv ? ldg32(in_al + v + kVB) : 0u;
+}
+
+// The thread's words from its loads: w[1..kVW] its own, w[0] the 4 bytes
+// before, w[kVW + 1] the 4 bytes after. Every lane of the warp calls it
+// (shuffles).
+__device__ __forceinline__ void block_words(const Raw &r, uint32_t lane, uint32_t (&w)[kVW + 2])
+{
+    w[1] = r.a.x; w[2] = r.a.y; w[3] = r.a.z; w[4] = r.a.w;
+    w[5] = r.b.x; w[6] = r.b.y; w[7] = r.b.z; w[8] = r.b.w;
     uint32_t prev = __shfl_up_sync(0xffffffffu, w[kVW], 1);
     uint32_t next = __shfl_down_sync(0xffffffffu, w[1], 1);
-    if (lane == 0) prev = v >= 4 && v - 4 < endv ? ldg32(in_al + v - 4) : 0u;
-    if (lane == 31) next = v + kVB < endv ? ldg32(in_al + v + kVB) : 0u;
+    if (lane == 0) prev = r.edge;
+    if (lane == 31) next = r.edge;
     w[0] = prev;
     w[kVW + 1] = next;
 }
@@ -188,20 +208,22 @@ __device__ __noinline__ unsigned long long exact8(const Words W, uint64_t v, uin
     return ~0ull;
 }
 
-__global__ void __launch_bounds__(kVThreads) validate8_kernel(const uint8_t *in_al, uint64_t head,
-                                                              uint64_t n,
-                                                              unsigned long long *err)
+__global__ void __launch_bounds__(kVThreads, kV8Blocks)
+    validate8_kernel(const uint8_t *in_al, uint64_t head, uint64_t n, unsigned long long *err)
 {
     const uint64_t lo = head, hi = head + n;
     const uint64_t endv = (hi + 15) & ~15ull;
     const uint64_t stride = (uint64_t)gridDim.x * kVThreads * kVB;
     const uint32_t lane = threadIdx.x & 31u;
+    uint64_t wb = ((uint64_t)blockIdx.x * kVThreads + (threadIdx.x & ~31u)) * kVB;
+    Raw cur;
+    fetch_block(in_al, wb + (uint64_t)lane * kVB, endv, lane, cur);
     // a warp's lanes step together (the loop bound is warp-uniform)
-    for (uint64_t wb = ((uint64_t)blockIdx.x * kVThreads + (threadIdx.x & ~31u)) * kVB; wb < endv;
-         wb += stride) {
+    for (; wb < endv; wb += stride) {
         const uint64_t v = wb + (uint64_t)lane * kVB;
         Words W;
-        load_block(in_al, v, endv, W.w);
+        block_words(cur, lane, W.w);
+        fetch_block(in_al, v + stride, endv, lane, cur);   // the next step's block
         mask_block8(W.w, v, lo, hi);
         // >= E0 and >= F0 leads anywhere in the warp (the look-behind word
         // included): without them their terms are dropped
@@ -230,15 +252,14 @@ __global__ void __launch_bounds__(kVThreads) validate8_kernel(const uint8_t *in_
 
 // ---- UTF-16 ----------------------------------------------------------------
 
-// Bit 15 of each 16-bit lane: the unit is a surrogate (D800-DFFF), a high one
-// (D800-DBFF), a low one (DC00-DFFF).
+// Bit 15 of each 16-bit lane: the unit is a surrogate (D800-DFFF); of those,
+// bit 10 of the unit (bit 15 of x << 5) tells a low one (DC00-DFFF) from a
+// high one (D800-DBFF).
 __device__ __forceinline__ uint32_t sur_lanes(uint32_t x)
 {
     const uint32_t v = (x & 0xF800F800u) ^ 0xD800D800u;
     return (v - 0x00010001u) & ~v & 0x80008000u;
 }
-__device__ __forceinline__ uint32_t hi_lanes(uint32_t x) { return sur_lanes(x) & ~(x << 5); }
-__device__ __forceinline__ uint32_t lo_lanes(uint32_t x) { return sur_lanes(x) & (x << 5); }
 
 // Unit i of the thread (i in [-2, 18)); w[0] holds units -2, -1.
 __device__ __forceinline__ uint32_t unit16(const uint32_t *w, int i)
@@ -263,20 +284,22 @@ __device__ __noinline__ unsigned long long exact16(const Words W, uint64_t u0, u
 // Units are counted from the 16-byte boundary at or before the input: the
 // input is units [lo, hi).
 template <bool kBE>
-__global__ void __launch_bounds__(kVThreads) validate16_kernel(const uint8_t *in_al, uint64_t lo,
-                                                               uint64_t n,
-                                                               unsigned long long *err)
+__global__ void __launch_bounds__(kVThreads, kV16Blocks)
+    validate16_kernel(const uint8_t *in_al, uint64_t lo, uint64_t n, unsigned long long *err)
 {
     const uint64_t hi = lo + n;
     const uint64_t endv = (2 * hi + 15) & ~15ull;   // bytes
     const uint64_t stride = (uint64_t)gridDim.x * kVThreads * kVB;
     const uint32_t lane = threadIdx.x & 31u;
-    for (uint64_t wb = ((uint64_t)blockIdx.x * kVThreads + (threadIdx.x & ~31u)) * kVB; wb < endv;
-         wb += stride) {
+    uint64_t wb = ((uint64_t)blockIdx.x * kVThreads + (threadIdx.x & ~31u)) * kVB;
+    Raw cur;
+    fetch_block(in_al, wb + (uint64_t)lane * kVB, endv, lane, cur);
+    for (; wb < endv; wb += stride) {
         const uint64_t v = wb + (uint64_t)lane * kVB;
         const uint64_t u0 = v / 2;   // the thread's first unit
         Words W;
-        load_block(in_al, v, endv, W.w);
+        block_words(cur, lane, W.w);
+        fetch_block(in_al, v + stride, endv, lane, cur);   // the next step's block
         if (u0 < lo + 2 || u0 + kVB / 2 + 2 > hi) {   // units outside the input read as zero
 #pragma unroll
             for (int j = 0; j < kVW + 2; j++) {
@@ -291,15 +314,29 @@ __global__ void __launch_bounds__(kVThreads) validate16_kernel(const uint8_t *in
             for (int j = 0; j < kVW + 2; j++) W.w[j] = prmt(W.w[j], 0, 0x2301);
         }
         // a unit is a low surrogate exactly when the unit before it is a high
-        // one (and the thread's last unit may be high only if a low follows)
-        uint32_t bad = 0, h_prev = hi_lanes(W.w[0]);
+        // one (and the thread's last unit may be high only if a low follows);
+        // with no surrogate among the thread's own units none of them is an
+        // error, and the pairing check is skipped
+        uint32_t sur[kVW + 2], any = 0;
 #pragma unroll
         for (int j = 1; j <= kVW; j++) {
-            const uint32_t h = hi_lanes(W.w[j]);
-            bad |= __funnelshift_l(h_prev, h, 16) ^ lo_lanes(W.w[j]);
-            h_prev = h;
+            sur[j] = sur_lanes(W.w[j]);
+            any |= sur[j];
         }
-        bad |= (h_prev ^ (lo_lanes(W.w[kVW + 1]) << 16)) & 0x80000000u;
+        uint32_t bad = 0;
+        if (any) {
+            sur[0] = sur_lanes(W.w[0]);
+            sur[kVW + 1] = sur_lanes(W.w[kVW + 1]);
+            uint32_t h_prev = sur[0] & ~(W.w[0] << 5);
+#pragma unroll
+            for (int j = 1; j <= kVW; j++) {
+                const uint32_t x5 = W.w[j] << 5;
+                const uint32_t h = sur[j] & ~x5;
+                bad |= __funnelshift_l(h_prev, h, 16) ^ (sur[j] & x5);
+                h_prev = h;
+            }
+            bad |= (h_prev ^ ((sur[kVW + 1] & (W.w[kVW + 1] << 5)) << 16)) & 0x80000000u;
+        }
         if (bad) {
             const unsigned long long key = exact16(W, u0, lo, hi);
             if (key != ~0ull) atomicMin(err, key);
@@ -321,22 +358,32 @@ __global__ void validate_result_kernel(unsigned long long *err, uint64_t n, Resu
     __threadfence_system();
 }
 
-int g_grid[64] = {0};
+// Resident CTAs over the GPU for the UTF-8 kernel ([0]) and the UTF-16
+// kernels ([1]), per device (each kernel fills the SMs at its own occupancy).
+int g_grid[64][2] = {};
 
-int validate_grid(int device)
+int validate_grid(int device, bool utf16)
 {
     if (device < 0 || device >= 64) return 0;
-    if (g_grid[device]) return g_grid[device];
-    int sms = 0, per8 = 0, per16 = 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per8, validate8_kernel, kVThreads, 0) !=
-            cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per16, validate16_kernel<true>, kVThreads,
-                                                      0) != cudaSuccess)
+    int &g = g_grid[device][utf16 ? 1 : 0];
+    if (g) return g;
+    int sms = 0, per = 0, per_be = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
         return 0;
-    const int per = per8 < per16 ? per8 : per16;
-    g_grid[device] = sms * (per > 0 ? per : 1);
-    return g_grid[device];
+    if (!utf16) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, validate8_kernel, kVThreads, 0) !=
+            cudaSuccess)
+            return 0;
+    } else {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, validate16_kernel<false>, kVThreads,
+                                                          0) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_be, validate16_kernel<true>,
+                                                          kVThreads, 0) != cudaSuccess)
+            return 0;
+        if (per_be < per) per = per_be;
+    }
+    g = sms * (per > 0 ? per : 1);
+    return g;
 }
 
 }  // namespace
@@ -346,7 +393,7 @@ cudaError_t launch_validate(const void *in, uint64_t n, bool utf16, bool big_end
 {
     int device = 0;
     if (cudaGetDevice(&device) != cudaSuccess) return cudaErrorInvalidDevice;
-    int grid = validate_grid(device);
+    int grid = validate_grid(device, utf16);
     if (grid <= 0) return cudaErrorInvalidValue;
     const uintptr_t p = reinterpret_cast<uintptr_t>(in);
     const uint8_t *in_al = reinterpret_cast<const uint8_t *>(p & ~(uintptr_t)15u);

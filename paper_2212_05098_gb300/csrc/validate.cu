@@ -23,6 +23,7 @@
 // because every earlier position is a validated character start or a
 // continuation inside one. A one-thread kernel then turns the key into the
 // call's result and resets it for the next call.
+#include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -360,13 +361,16 @@ __global__ void validate_result_kernel(unsigned long long *err, uint64_t n, Resu
 
 // Resident CTAs over the GPU for the UTF-8 kernel ([0]) and the UTF-16
 // kernels ([1]), per device (each kernel fills the SMs at its own occupancy).
-int g_grid[64][2] = {};
+// Calls from several host threads may fill an entry at once; they store the
+// same value.
+std::atomic<int> g_grid[64][2] = {};
 
 int validate_grid(int device, bool utf16)
 {
     if (device < 0 || device >= 64) return 0;
-    int &g = g_grid[device][utf16 ? 1 : 0];
-    if (g) return g;
+    std::atomic<int> &g = g_grid[device][utf16 ? 1 : 0];
+    const int known = g.load(std::memory_order_relaxed);
+    if (known) return known;
     int sms = 0, per = 0, per_be = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
         return 0;
@@ -382,8 +386,9 @@ int validate_grid(int device, bool utf16)
             return 0;
         if (per_be < per) per = per_be;
     }
-    g = sms * (per > 0 ? per : 1);
-    return g;
+    const int grid = sms * (per > 0 ? per : 1);
+    g.store(grid, std::memory_order_relaxed);
+    return grid;
 }
 
 }  // namespace

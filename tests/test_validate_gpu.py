@@ -90,6 +90,32 @@ def test_utf16_errors_at_block_edges(ctx):
             _check16(ctx, data, off, be=True)
 
 
+def test_utf16_surrogates_in_bmp_text(ctx):
+    """Surrogates alone in text without them (threads holding no surrogate
+    skip the pairing check): lone halves and valid pairs at the edges of a
+    thread's 16 units, a warp's 512 and a CTA's 4096, with their neighbours
+    surrogate-free."""
+    base = textgen.generate("cjk", N, textgen.UTF16, seed=166).data
+    units = N // 2
+    rng = np.random.default_rng(167)
+    edges = [0, 1, 14, 15, 16, 17, 31, 32, 511, 512, 4095, 4096, units - 2, units - 1]
+    for e in edges:
+        for case in ("high", "low", "pair", "pair+lone"):
+            data = base.copy()
+            w = data.view("<u2")
+            if case == "high":
+                w[e] = 0xDBFF
+            elif case == "low":
+                w[e] = 0xDC00
+            elif e + 1 < units:
+                w[e], w[e + 1] = 0xD83D, 0xDE00     # valid: no error
+                if case == "pair+lone" and e + 3 < units:
+                    w[e + 3] = 0xDFFF                # a lone low two units on
+            off = 2 * int(rng.integers(0, 8))
+            _check16(ctx, data, off)
+            _check16(ctx, data, off, be=True)
+
+
 def test_random_and_corrupted(ctx):
     for i in range(12):
         d = textgen.random_bytes(N + 977 * i, seed=170 + i)
